@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the multipole Poisson solve on one GB300 (or N replicas).
+
+Workload: presupernova-like core, 512 x 128 x 256 cells (geometric shells over
+[1e5, 1e10] cm), l_max = 16, density rho_c/(1+(r/r_c)^2)^1.5 times seeded
+l <= 4 harmonic perturbations (seed 2).  One step = one full solve (moments,
+radial recurrences, potential) of that density, resident in HBM, through the
+C ABI (mp_solve) on the split-precision BF16x3 tensor-core path.
+
+Also reported on the same line: the float64 GPU path on the same workload,
+the accuracy of both against the FP64 CPU oracle, an end-to-end number with
+host buffers (mp_solve_host: host->device copy of rho, solve, device->host copy
+of Phi), per-kernel timing with the dominant kernel's HBM roofline fraction,
+SM clocks sampled during the timed region, and the oracle timed on the host
+cores as a CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 the script runs under torch.distributed.run, one rank per GPU, each
+rank solving its own replica of the workload (no data exchange); the job value
+is the total solves/s over ranks timed by the slowest rank.  --impl reference
+times the FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solves/s & Gcell*mode/s, BF16x3 vs FP64 GPU at <=1e-6 rel err in Phi"
+WORKLOAD = "presupernova core 512x128x256 cells, geometric r in [1e5,1e10] cm, l_max=16, seed 2"
+SPLIT_PRECISION = "bf16x3"
+
+# DRAM bytes (read + write) per launch from one ncu capture of the same
+# workload, valid while the kernel source hashes match.
+NCU_TRAFFIC = {
+    # kernel name: (bytes per launch, sha1 of csrc/mp_split.cu at capture time)
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10000)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU-baseline budget")
+    return p.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    with open(os.path.join(ROOT, "paper_2602_02507_gb300", "csrc", "mp_split.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            import torch
+            bus = None
+            props = torch.cuda.get_device_properties(self.dev)
+            if hasattr(props, "pci_bus_id"):
+                bus = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id,
+                                            getattr(props, "pci_device_id", 0))
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if bus:
+                cmd += ["--id=" + bus]
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception as e:  # no nvidia-smi: clocks stay unknown
+            log("clock sampler unavailable:", e)
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                    power.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------- oracle timing
+def time_oracle(w, budget_s: float, max_reps: int = 200):
+    from oracle import oracle as O
+    m = w.mesh
+    tab = O.build_tables(m.r, m.theta, m.phi, m.L)
+    O.solve(tab, w.rho, m.G)  # warm caches and threads
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        O.solve(tab, w.rho, m.G)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= max_reps:
+            break
+    return reps / el, reps, el, O.get_threads()
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    from oracle import build as oracle_build
+    from oracle import oracle as O
+    from paper_2602_02507_gb300 import workloads as W
+    oracle_build.build()
+    w = W.presn()
+    m = w.mesh
+    tab = O.build_tables(m.r, m.theta, m.phi, m.L)
+    for _ in range(args.warmup):
+        O.solve(tab, w.rho, m.G)
+    steps = max(1, min(args.steps, 30))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        O.solve(tab, w.rho, m.G)
+    el = time.perf_counter() - t0
+    value = steps / el
+    sample = f"the whole workload per step: factored FP64 oracle solve, tables prebuilt, {steps} steps"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)", "cells": m.cells, "l_max": m.L},
+        "gcell_mode_per_s": value * m.cells * m.KL / 1e9,
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": O.get_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def alg_bytes(kernel: str, cells: int, rows: int, n_r: int, L: int, KL: int):
+    """Algorithmic DRAM bytes per launch (each input read once, each output written once)."""
+    P = 2 * L + 1
+    table = {
+        "split_phi_project_tc": 8 * cells + 4 * rows * P,        # rho in, F out (float32, 2L+1 columns)
+        "split_synth_tc": 8 * cells,                             # Phi out (coefficients are L2-resident)
+        "split_theta_contract": 4 * rows * P + 8 * n_r * KL,     # F in, moments out
+        "radial_scan": 8 * n_r * KL * 2 + 16 * (n_r + 1) * KL + 4 * n_r * KL,  # A in; C, MR, MI, C32 out
+        "fp64_phi_project": 8 * cells + 8 * rows * P,
+        "fp64_theta_contract": 8 * rows * P + 8 * n_r * KL,
+        "fp64_theta_synth": 8 * rows * P,
+        "fp64_phi_synth": 8 * cells + 8 * rows * P,
+    }
+    return table.get(kernel)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2602_02507_gb300 import multipole as mpl
+    from paper_2602_02507_gb300 import workloads as W
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = W.presn()
+    m = w.mesh
+    cells, KL = m.cells, m.KL
+    rows = m.shape[0] * m.shape[1]
+    stream = torch.cuda.current_stream()
+    rho = torch.from_numpy(w.rho).cuda()
+    phi = torch.empty_like(rho)
+    phi64 = torch.empty_like(rho)
+    mesh = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=SPLIT_PRECISION, stream=stream)
+    mesh64 = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="fp64", stream=stream)
+    for ms_, out in ((mesh, phi), (mesh64, phi64)):
+        ms_.set_density(rho)
+        ms_.set_phi_output(out)
+        ms_.solve()
+        ms_.synchronize()
+
+    # accuracy against the FP64 CPU oracle (rank 0) and between the GPU paths
+    acc = {"tolerance": 1e-6}
+    p_split = phi.cpu().numpy()
+    p64 = phi64.cpu().numpy()
+    acc["phi_max_rel_err_split_vs_fp64_gpu"] = float(np.max(np.abs(p_split - p64) / np.abs(p64)))
+    cpu = None
+    if rank == 0:
+        from oracle import oracle as O
+        tab = O.build_tables(m.r, m.theta, m.phi, m.L)
+        ref = O.solve(tab, w.rho, m.G)["phi"]
+        acc["phi_max_rel_err_split_vs_oracle"] = float(np.max(np.abs(p_split - ref) / np.abs(ref)))
+        acc["phi_max_rel_err_fp64_gpu_vs_oracle"] = float(np.max(np.abs(p64 - ref) / np.abs(ref)))
+        if world == 1:
+            v, reps, el, cores = time_oracle(w, args.cpu_seconds)
+            cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{reps} whole-workload solves (factored FP64 oracle, tables prebuilt) in {el:.1f} s"}
+
+    # ---- timed region: split path, K solves, per-kernel events on the mesh stream
+    for _ in range(args.warmup):
+        mesh.solve()
+    mesh.synchronize()
+    mesh.profile(True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        mesh.solve()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    mesh.synchronize()
+    local_ms = ev0.elapsed_time(ev1)
+    total_ms = max_over_ranks(local_ms)
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms * 1e-3)
+
+    # ---- float64 GPU path on the same workload
+    k64 = max(3, min(args.steps // 50, 200))
+    for _ in range(2):
+        mesh64.solve()
+    mesh64.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k64):
+        mesh64.solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(e0.elapsed_time(e1)) / k64
+    mesh64.synchronize()
+
+    # ---- end to end through the C ABI with pinned host buffers
+    rho_h = torch.from_numpy(w.rho).pin_memory()
+    phi_h = torch.empty_like(rho_h).pin_memory()
+    ke = max(3, min(args.steps // 100, 100))
+    mesh.solve_host_ptr(rho_h.data_ptr(), phi_h.data_ptr())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        mesh.solve_host_ptr(rho_h.data_ptr(), phi_h.data_ptr())
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_err = float(np.max(np.abs(phi_h.numpy() - p_split)))
+
+    # ---- roofline of the dominant kernel
+    log("kernels:", json.dumps(prof))
+    dom = max(prof, key=lambda k: prof[k]["total_ms"])
+    avg_ms = prof[dom]["total_ms"] / prof[dom]["launches"]
+    nbytes = alg_bytes(dom, cells, rows, m.shape[0], m.L, KL)
+    peak, peak_kind = measured_peaks()
+    achieved = nbytes / (avg_ms * 1e-3) / 1e9
+    traffic = None
+    rec = NCU_TRAFFIC.get(dom)
+    if rec and rec[1] == source_hash():
+        traffic = rec[0]
+    kernels = {k: {"launches": v["launches"], "avg_us": 1e3 * v["total_ms"] / v["launches"],
+                   "share": v["total_ms"] / sum(x["total_ms"] for x in prof.values())} for k, v in prof.items()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": SPLIT_PRECISION, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells, "l_max": m.L, "moments": KL,
+                       "precision": SPLIT_PRECISION, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (rho 134 MB + Phi 134 MB per step)"},
+            "gcell_mode_per_s": value * cells * KL / 1e9,
+            "fp64_gpu": {"solves_per_s": world / (ms64 * 1e-3), "ms_per_solve": ms64, "steps": k64,
+                         "gcell_mode_per_s": world / (ms64 * 1e-3) * cells * KL / 1e9},
+            "speedup_split_vs_fp64_gpu": ms64 / ms_per_step,
+            "accuracy": acc,
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "algorithmic_bytes": nbytes, "avg_launch_us": avg_ms * 1e3},
+            "kernels": kernels,
+            "e2e": {"value": world * ke / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * cells,
+                    "d2h_bytes_per_step": 8 * cells, "steps": ke, "max_abs_diff_vs_device_solve": e2e_err},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    mesh.close()
+    mesh64.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

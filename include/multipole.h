@@ -1,0 +1,220 @@
+/*
+ * multipole.h -- C ABI of the GB300 multipole Poisson solver.
+ *
+ * Solves nabla^2 Phi = S, S = 4 pi G rho, for an isolated source on a spherical
+ * (r, theta, phi) mesh with the multipole method of GenASiS II (Cardall,
+ * Budiardja, Murphy & Endeve), Sec. 2.2:
+ *   (a) angular moments of each radial shell, Eq. (AngularMomentsDiscrete),
+ *       with cell-averaged real kernels A^c_lm = P~_l^m cos(m phi),
+ *       A^s_lm = P~_l^m sin(m phi), Eqs. (AngularKernel_c), (AngularKernel_s);
+ *   (b) weighting by the shell integrals of r^l and r^-(l+1),
+ *       Eqs. (RadialRegular), (RadialIrregular);
+ *   (c) outward (regular) and inward (irregular) radial recurrences on the
+ *       n_r + 1 shell edges;
+ *   (d) the potential at every cell, Eq. (Solution), from the edge moments
+ *       interpolated to the cell centre.
+ * All compute runs in CUDA kernels on the device; there is no CPU fallback.
+ *
+ * Layouts (C row-major, float64 unless stated):
+ *   rho, phi       [n_r][n_theta][n_phi]
+ *   moments        [n_r][K_L]         K_L = (L+1)^2 real moments per shell
+ *   edge moments   [n_r + 1][K_L]
+ *   moment index   q(l,m,a) = l*l + p(m,a), p(0,c) = 0, p(m,c) = 2m-1,
+ *                  p(m,s) = 2m (m >= 1); the (m = 0, sine) kernel vanishes
+ *                  identically and is not carried.
+ *
+ * Conventions the paper leaves open (each is documented with the library):
+ *   - cell averages of the angular kernels are solid-angle means and those of
+ *     the radial kernels volume means;
+ *   - "linear interpolation to the cell center" uses the coordinate midpoint;
+ *   - radial kernels are scaled by r_ref = sqrt(r_min+ * r_max) (r_min+ the
+ *     smallest positive edge): R^R -> (r/r_ref)^l, R^I -> r_ref^l / r^(l+1); the
+ *     exported edge moments M^R, M^I carry that scaling, Phi does not depend
+ *     on it;
+ *   - a shell touching r = 0 replaces, for l >= 2, its divergent own-shell
+ *     term by 6 r_1^2 / (5 (l + 3)) times the shell's moment (the exact volume
+ *     mean for a moment uniform inside the ball); M^I at edge 0 then excludes
+ *     that shell's own term.
+ *
+ * Threading and ordering: a mesh is bound to one CUDA stream; every call that
+ * touches the device is enqueued on it and returns without waiting unless its
+ * comment says otherwise.  Calls on one mesh must not run concurrently from
+ * several host threads.  Device-side errors (non-finite density, a wait that
+ * ran out of time) are recorded on the device and reported by the next
+ * mp_mesh_synchronize() or mp_solve_host().
+ *
+ * Errors: every function returns an mp_status.  Argument errors are detected on
+ * the host before anything is enqueued and leave the mesh unchanged.
+ * mp_last_error_detail() gives a one-line explanation of the last error raised
+ * on the calling host thread.
+ */
+#ifndef GB300_MULTIPOLE_H
+#define GB300_MULTIPOLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MP_API __attribute__((visibility("default")))
+#else
+#define MP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mp_mesh mp_mesh;   /* opaque, library-owned */
+typedef struct mp_batch mp_batch; /* opaque, library-owned */
+
+typedef enum {
+    MP_OK = 0,
+    MP_ERR_INVALID_ARG = 1, /* a pointer, size or edge array is unusable            */
+    MP_ERR_RANGE = 2,       /* r^l or r^-(l+1) would leave the float64 range         */
+    MP_ERR_CUDA = 3,        /* a CUDA runtime call failed                           */
+    MP_ERR_OOM = 4,         /* device or host allocation failed                     */
+    MP_ERR_NOT_READY = 5,   /* no density bound yet                                 */
+    MP_ERR_NONFINITE = 6,   /* the density held a NaN or an infinity                */
+    MP_ERR_TIMEOUT = 7,     /* a device-side wait gave up (pipeline stalled)         */
+    MP_ERR_UNSUPPORTED = 8  /* valid request this build cannot serve (see detail)   */
+} mp_status;
+
+typedef enum {
+    MP_PREC_FP64 = 0,   /* every step in float64 on CUDA cores                       */
+    MP_PREC_BF16X3 = 1, /* angular contractions as split-bf16 tensor-core GEMMs,     */
+                        /* density deviations in 2 bf16 terms, tables in 3           */
+    MP_PREC_BF16X6 = 2  /* as BF16X3 with 3 bf16 terms on both operands              */
+} mp_precision;
+
+/* Sizes and the effective configuration of a mesh (mp_mesh_get_info). */
+typedef struct {
+    int n_r, n_theta, n_phi, l_max;
+    int n_moments;           /* K_L = (l_max + 1)^2                                  */
+    int precision;           /* requested mp_precision                               */
+    int effective_precision; /* what solve runs: split meshes with odd n_phi run FP64 */
+    double r_ref;            /* reference radius of the radial kernel scaling        */
+    double G;                /* gravitational constant, S = 4 pi G rho               */
+    size_t device_bytes;     /* device memory the mesh holds (tables + workspace)    */
+} mp_mesh_info;
+
+/*
+ * Create a mesh and build its tables on the device in float64 (Sec. 2.2: the
+ * cell-averaged angular kernels and the analytically averaged radial kernels
+ * are computed once and stored).
+ *   r_edges      host, n_r + 1 values, strictly increasing, r_edges[0] >= 0.
+ *   theta_edges  host, n_theta + 1 values, strictly increasing within [0, pi].
+ *   phi_edges    host, n_phi + 1 values, strictly increasing, span <= 2 pi.
+ *                (The source is taken to vanish outside the meshed angles.)
+ *   l_max        0 <= l_max <= 128; the split precisions need 2 l_max + 1 <= 256.
+ *   G            gravitational constant (> 0).
+ *   prec         mp_precision.
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default stream).
+ *   out          receives the mesh; unchanged on error.
+ * The edge arrays are copied.  Blocks until the tables are built.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_RANGE, MP_ERR_OOM, MP_ERR_CUDA.
+ */
+MP_API mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edges, int n_theta,
+                         const double *phi_edges, int n_phi, int l_max, double G, mp_precision prec,
+                         void *cuda_stream, mp_mesh **out);
+
+/* Release the mesh and every device buffer it owns (waits for its stream). */
+MP_API mp_status mp_mesh_destroy(mp_mesh *mesh);
+
+/* Rebind the mesh to another stream (waits for work on the old one first). */
+MP_API mp_status mp_mesh_set_stream(mp_mesh *mesh, void *cuda_stream);
+
+/* Sizes and configuration; host only, never touches the device. */
+MP_API mp_status mp_mesh_get_info(const mp_mesh *mesh, mp_mesh_info *info);
+
+/*
+ * Bind the density: device pointer to n_r * n_theta * n_phi float64 values in
+ * the rho layout.  Nothing is copied: the buffer is read by each later
+ * mp_solve() and must stay valid until then.  Caller owns it.
+ */
+MP_API mp_status mp_set_density(mp_mesh *mesh, const double *rho_dev);
+
+/*
+ * Bind the output: device pointer to n_r * n_theta * n_phi float64 values that
+ * later mp_solve() calls write Phi into (caller owns it).  NULL makes the mesh
+ * write into a buffer of its own, allocated on first use.
+ */
+MP_API mp_status mp_set_phi_output(mp_mesh *mesh, double *phi_dev);
+
+/*
+ * Run steps (a)-(d) on the mesh's stream: reads the bound density, writes Phi
+ * and keeps the moments of this solve for mp_get_moments().
+ * Errors: MP_ERR_NOT_READY (no density bound), MP_ERR_OOM, MP_ERR_CUDA;
+ * device-side errors surface at mp_mesh_synchronize().
+ */
+MP_API mp_status mp_solve(mp_mesh *mesh);
+
+/*
+ * Copy the last Phi into phi_dev (device pointer, rho layout).  A no-op when
+ * phi_dev is the bound output buffer.  Stream-ordered.
+ */
+MP_API mp_status mp_get_phi(mp_mesh *mesh, double *phi_dev);
+
+/*
+ * Copy the moments of the last solve (device pointers; any may be NULL):
+ *   ang_dev [n_r][K_L]      angular moments of step (a), Eq. (AngularMomentsDiscrete)
+ *   mr_dev  [n_r + 1][K_L]  regular (outward) edge moments of step (c)
+ *   mi_dev  [n_r + 1][K_L]  irregular (inward) edge moments of step (c)
+ * Stream-ordered.
+ */
+MP_API mp_status mp_get_moments(mp_mesh *mesh, double *ang_dev, double *mr_dev, double *mi_dev);
+
+/*
+ * End-to-end solve from host memory: copies rho_host to the device, solves,
+ * copies Phi back into phi_host and waits for completion (both host arrays in
+ * the rho layout; pinned memory gives the fastest copies).  Returns any
+ * device-side error of the solve.
+ */
+MP_API mp_status mp_solve_host(mp_mesh *mesh, const double *rho_host, double *phi_host);
+
+/* Wait for the mesh's stream and return (then clear) any device-side error. */
+MP_API mp_status mp_mesh_synchronize(mp_mesh *mesh);
+
+/*
+ * Per-kernel timing on the mesh's stream (CUDA events around each launch).
+ * mp_profile_enable(mesh, 1) starts recording (and resets totals);
+ * mp_profile_read() waits for the stream, then fills up to cap entries with
+ * kernel names (static strings), launch counts and total milliseconds and
+ * returns the number of distinct kernels in *n_out.
+ */
+MP_API mp_status mp_profile_enable(mp_mesh *mesh, int enable);
+MP_API mp_status mp_profile_read(mp_mesh *mesh, const char **names, int *launches, double *total_ms, int cap,
+                          int *n_out);
+
+/*
+ * Batched solves: many meshes (uneven sizes and l_max, each with its density
+ * and output bound) solved together.  The first mesh's stream is used.  The
+ * whole batch is replayed as one captured CUDA graph after the first solve.
+ *   meshes  host array of count mesh pointers (borrowed: they must outlive
+ *           the batch and keep their bindings).
+ */
+MP_API mp_status mp_batch_create(mp_mesh *const *meshes, int count, mp_batch **out);
+MP_API mp_status mp_batch_solve(mp_batch *batch);
+MP_API mp_status mp_batch_destroy(mp_batch *batch);
+
+/*
+ * Pick tile and launch parameters for the mesh by timing candidates on the
+ * device (needs a bound density and output); the choice is cached in
+ * cache_path (a text file, may be NULL) keyed by (n_r, n_theta, n_phi, l_max,
+ * precision) and reused by later meshes of the same key.
+ */
+MP_API mp_status mp_autotune(mp_mesh *mesh, const char *cache_path);
+
+/* Static description of a status code. */
+MP_API const char *mp_status_string(mp_status status);
+
+/* Copies the last error detail of this host thread into buf (NUL-terminated). */
+MP_API mp_status mp_last_error_detail(char *buf, int len);
+
+/* Library version, as major * 10000 + minor * 100 + patch. */
+MP_API int mp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_MULTIPOLE_H */

@@ -1,0 +1,789 @@
+// mp_api.cu -- the C ABI of include/multipole.h: argument checks, device
+// memory, TMA descriptors, dispatch of the float64 and split-precision paths,
+// per-kernel timing, graph-captured batches and the launch-parameter tuner.
+#include <cudaTypedefs.h>
+
+#include <cfloat>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "mp_internal.h"
+
+namespace mp {
+
+namespace {
+thread_local char g_detail[512] = "";
+constexpr double kPi = 3.14159265358979323846;
+}  // namespace
+
+mp_status set_error(mp_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+static mp_status cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return MP_OK;
+    cudaGetLastError();  // clear a sticky launch error of this thread
+    return set_error(e == cudaErrorMemoryAllocation ? MP_ERR_OOM : MP_ERR_CUDA, "%s: %s", what,
+                     cudaGetErrorString(e));
+}
+
+#define MP_TRY(call)                                        \
+    do {                                                    \
+        mp_status st_ = cuda_status((call), #call);         \
+        if (st_ != MP_OK) return st_;                       \
+    } while (0)
+
+// ---------------------------------------------------------------- profiling
+static cudaEvent_t pool_get(mp_mesh *m)
+{
+    if (!m->event_pool.empty()) {
+        cudaEvent_t e = m->event_pool.back();
+        m->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(mp_mesh *m, const char *name, cudaEvent_t *ev)
+{
+    (void)name;
+    *ev = nullptr;
+    if (!m->profiling) return;
+    *ev = pool_get(m);
+    cudaEventRecord(*ev, m->stream);
+}
+
+void prof_end(mp_mesh *m, const char *name, cudaEvent_t ev0)
+{
+    if (!m->profiling || !ev0) return;
+    cudaEvent_t ev1 = pool_get(m);
+    cudaEventRecord(ev1, m->stream);
+    m->prof_pending.push_back({name, {ev0, ev1}});
+}
+
+static void prof_collect(mp_mesh *m)
+{
+    for (auto &pe : m->prof_pending) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, pe.second.first, pe.second.second);
+        ProfileEntry &e = m->prof[pe.first];
+        e.name = pe.first;
+        e.launches += 1;
+        e.total_ms += ms;
+        m->event_pool.push_back(pe.second.first);
+        m->event_pool.push_back(pe.second.second);
+    }
+    m->prof_pending.clear();
+}
+
+// ---------------------------------------------------------------- TMA descriptors
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// [rows][cols] float64, 128-byte swizzled boxes of [box_rows][16].
+static mp_status make_map(CUtensorMap *map, const void *ptr, long long rows, int cols, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return set_error(MP_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (reinterpret_cast<uintptr_t>(ptr) & 15)
+        return set_error(MP_ERR_INVALID_ARG, "split precision needs 16-byte aligned density/potential buffers");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(double)};
+    cuuint32_t box[2] = {16u, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1u, 1u};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(ptr), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(MP_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return MP_OK;
+}
+
+// ---------------------------------------------------------------- helpers
+static bool finite_increasing(const double *e, int n)
+{
+    for (int i = 0; i <= n; ++i)
+        if (!std::isfinite(e[i])) return false;
+    for (int i = 0; i < n; ++i)
+        if (!(e[i + 1] > e[i])) return false;
+    return true;
+}
+
+template <class T>
+static mp_status dalloc(mp_mesh *m, T **p, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_error(MP_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    m->device_bytes += count * sizeof(T);
+    return MP_OK;
+}
+
+static void free_mesh_buffers(mp_mesh *m)
+{
+    void *ptrs[] = {m->d_r,   m->d_Ith,  m->d_dmu,    m->d_Iph,   m->d_Iphc,   m->d_WR,    m->d_WI,
+                    m->d_RR,  m->d_RI,   m->d_V,      m->d_A,     m->d_MR,     m->d_MI,    m->d_C,
+                    m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_IthT32, m->d_Itc32, m->d_colsum,
+                    m->d_tabB, m->d_tabT, m->phi_own, m->rho_stage, m->d_err};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto &pe : m->prof_pending) {
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    for (cudaEvent_t e : m->event_pool) cudaEventDestroy(e);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static mp_status ensure_phi_own(mp_mesh *m)
+{
+    if (m->phi_own) return MP_OK;
+    return dalloc(m, &m->phi_own, (size_t)m->N);
+}
+
+static mp_status run_solve(mp_mesh *m, const double *rho, double *phi)
+{
+    if (m->eff_prec == MP_PREC_FP64) {
+        MP_TRY(launch_fp64_project(m, rho));
+        MP_TRY(launch_fp64_theta(m));
+        MP_TRY(launch_scan(m, 0));
+        MP_TRY(launch_fp64_synth(m, phi));
+    } else {
+        if (m->tm_rho_ptr != rho) {
+            mp_status st = make_map(&m->tm_rho, rho, m->R, m->n_p, 128);
+            if (st != MP_OK) return st;
+            m->tm_rho_ptr = rho;
+        }
+        if (m->tm_phi_ptr != phi) {
+            mp_status st = make_map(&m->tm_phi, phi, m->R, m->n_p, 32);
+            if (st != MP_OK) return st;
+            m->tm_phi_ptr = phi;
+        }
+        MP_TRY(launch_split_project(m, rho));
+        MP_TRY(launch_split_theta(m));
+        MP_TRY(launch_scan(m, 1));
+        MP_TRY(launch_split_synth(m, phi));
+    }
+    m->solved = 1;
+    return MP_OK;
+}
+
+static mp_status plan_split(mp_mesh *m)
+{
+    SplitPlan &pl = m->plan;
+    pl.a_terms = (m->prec == MP_PREC_BF16X6) ? 3 : 2;
+    pl.n_products = (m->prec == MP_PREC_BF16X6) ? 6 : 3;
+    pl.Npad = round_up(m->P, 16);
+    pl.n_kc = (m->n_p + 15) / 16;
+    pl.Kpad = std::max(16, round_up(2 * m->L, 16));
+    pl.NC = std::min(256, round_up(m->n_p, 16));
+    pl.n_nc = (m->n_p + pl.NC - 1) / pl.NC;
+    pl.proj_ctas = m->num_sms;
+    pl.synth_ctas = m->num_sms;
+    if (split_smem_limits(m) != 0)
+        return set_error(MP_ERR_UNSUPPORTED, "split-precision tiles of l_max = %d do not fit in shared memory", m->L);
+    return MP_OK;
+}
+
+}  // namespace mp
+
+using namespace mp;
+
+extern "C" {
+
+int mp_version(void) { return 100; }
+
+const char *mp_status_string(mp_status s)
+{
+    switch (s) {
+    case MP_OK: return "MP_OK";
+    case MP_ERR_INVALID_ARG: return "MP_ERR_INVALID_ARG: invalid argument";
+    case MP_ERR_RANGE: return "MP_ERR_RANGE: radial kernels leave the float64 range";
+    case MP_ERR_CUDA: return "MP_ERR_CUDA: CUDA runtime error";
+    case MP_ERR_OOM: return "MP_ERR_OOM: out of memory";
+    case MP_ERR_NOT_READY: return "MP_ERR_NOT_READY: no density bound";
+    case MP_ERR_NONFINITE: return "MP_ERR_NONFINITE: density holds NaN or infinity";
+    case MP_ERR_TIMEOUT: return "MP_ERR_TIMEOUT: a device-side wait gave up";
+    case MP_ERR_UNSUPPORTED: return "MP_ERR_UNSUPPORTED: request not supported";
+    }
+    return "unknown mp_status";
+}
+
+mp_status mp_last_error_detail(char *buf, int len)
+{
+    if (!buf || len <= 0) return MP_ERR_INVALID_ARG;
+    snprintf(buf, (size_t)len, "%s", g_detail);
+    return MP_OK;
+}
+
+mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edges, int n_theta,
+                         const double *phi_edges, int n_phi, int l_max, double G, mp_precision prec, void *cuda_stream,
+                         mp_mesh **out)
+{
+    g_detail[0] = 0;
+    if (!out) return set_error(MP_ERR_INVALID_ARG, "out is NULL");
+    if (!r_edges || !theta_edges || !phi_edges) return set_error(MP_ERR_INVALID_ARG, "edge array is NULL");
+    if (n_r < 1 || n_theta < 1 || n_phi < 1) return set_error(MP_ERR_INVALID_ARG, "mesh needs at least one cell per dimension");
+    if (l_max < 0 || l_max > 128) return set_error(MP_ERR_INVALID_ARG, "l_max must be in [0, 128]");
+    if (!(G > 0.0) || !std::isfinite(G)) return set_error(MP_ERR_INVALID_ARG, "G must be positive and finite");
+    if (prec != MP_PREC_FP64 && prec != MP_PREC_BF16X3 && prec != MP_PREC_BF16X6)
+        return set_error(MP_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if ((long long)n_r * n_theta * (long long)n_phi > (1LL << 40))
+        return set_error(MP_ERR_INVALID_ARG, "mesh too large");
+    if (!finite_increasing(r_edges, n_r) || r_edges[0] < 0.0)
+        return set_error(MP_ERR_INVALID_ARG, "radial edges must be finite, >= 0 and strictly increasing");
+    if (!finite_increasing(theta_edges, n_theta) || theta_edges[0] < -1e-12 || theta_edges[n_theta] > kPi + 1e-12)
+        return set_error(MP_ERR_INVALID_ARG, "polar edges must be strictly increasing within [0, pi]");
+    if (!finite_increasing(phi_edges, n_phi) || phi_edges[n_phi] - phi_edges[0] > 2.0 * kPi * (1.0 + 1e-12))
+        return set_error(MP_ERR_INVALID_ARG, "azimuthal edges must be strictly increasing and span at most 2 pi");
+    if (prec != MP_PREC_FP64 && 2 * l_max + 1 > 256)
+        return set_error(MP_ERR_UNSUPPORTED, "split precision supports l_max <= 127");
+
+    // reference radius and float64 range of the scaled radial kernels
+    const double rmin = r_edges[0] > 0.0 ? r_edges[0] : r_edges[1];
+    const double rmax = r_edges[n_r];
+    const double r_ref = std::sqrt(rmin * rmax);
+    {
+        const double lx_hi = std::log10(rmax / r_ref), lx_lo = std::log10(rmin / r_ref), lr = std::log10(r_ref);
+        const double e_reg = 3.0 * lr + (l_max + 3.0) * lx_hi;
+        const double e_irr = 2.0 * lr + std::max(0.0, (l_max - 2.0)) * (-lx_lo);
+        if (e_reg > 290.0 || e_irr > 290.0 || 3.0 * std::log10(rmax) > 300.0)
+            return set_error(MP_ERR_RANGE, "r^l or r^-(l+1) over [%g, %g] at l_max = %d exceeds float64", rmin, rmax,
+                             l_max);
+    }
+
+    mp_mesh *m = new (std::nothrow) mp_mesh();
+    if (!m) return set_error(MP_ERR_OOM, "host allocation failed");
+    m->n_r = n_r;
+    m->n_t = n_theta;
+    m->n_p = n_phi;
+    m->L = l_max;
+    m->KL = (l_max + 1) * (l_max + 1);
+    m->P = 2 * l_max + 1;
+    m->T = (l_max + 1) * (l_max + 2) / 2;
+    m->R = (long long)n_r * n_theta;
+    m->N = m->R * n_phi;
+    m->G = G;
+    m->r_ref = r_ref;
+    m->prec = prec;
+    m->origin = (r_edges[0] == 0.0);
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    m->h_r.assign(r_edges, r_edges + n_r + 1);
+    m->h_th.assign(theta_edges, theta_edges + n_theta + 1);
+    m->h_ph.assign(phi_edges, phi_edges + n_phi + 1);
+
+    auto fail = [&](mp_status st) {
+        free_mesh_buffers(m);
+        delete m;
+        return st;
+    };
+    if (cudaGetDevice(&m->device) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "cudaGetDevice"));
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, m->device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, m->device);
+
+    // split precision runs where its TMA tiles apply; otherwise float64
+    m->eff_prec = prec;
+    if (prec != MP_PREC_FP64 && (n_phi % 2 != 0 || n_phi < 16 || m->R < 128)) m->eff_prec = MP_PREC_FP64;
+    if (m->eff_prec != MP_PREC_FP64 && !(major == 10 && minor == 3))
+        return fail(set_error(MP_ERR_UNSUPPORTED, "split precision needs an sm_103 device (found sm_%d%d)", major, minor));
+
+    const size_t nedges = (size_t)(n_r + 1) + (n_theta + 1) + (n_phi + 1);
+    mp_status st;
+#define ALLOC(ptr, count)                             \
+    st = dalloc(m, &(ptr), (size_t)(count));          \
+    if (st != MP_OK) return fail(st);
+    ALLOC(m->d_r, nedges);
+    ALLOC(m->d_Ith, (size_t)m->T * n_theta);
+    ALLOC(m->d_dmu, n_theta);
+    ALLOC(m->d_Iph, (size_t)m->P * n_phi);
+    ALLOC(m->d_Iphc, (size_t)m->P * n_phi);
+    ALLOC(m->d_WR, (size_t)(l_max + 1) * n_r);
+    ALLOC(m->d_WI, (size_t)(l_max + 1) * n_r);
+    ALLOC(m->d_RR, (size_t)(l_max + 1) * n_r);
+    ALLOC(m->d_RI, (size_t)(l_max + 1) * n_r);
+    ALLOC(m->d_V, n_r);
+    ALLOC(m->d_A, (size_t)n_r * m->KL);
+    ALLOC(m->d_MR, (size_t)(n_r + 1) * m->KL);
+    ALLOC(m->d_MI, (size_t)(n_r + 1) * m->KL);
+    ALLOC(m->d_C, (size_t)n_r * m->KL);
+    ALLOC(m->d_err, 1);
+    if (m->eff_prec == MP_PREC_FP64) {
+        ALLOC(m->d_F64, (size_t)m->R * m->P);
+        ALLOC(m->d_G64, (size_t)m->R * m->P);
+    } else {
+        st = plan_split(m);
+        if (st != MP_OK) return fail(st);
+        const SplitPlan &pl = m->plan;
+        ALLOC(m->d_F32, (size_t)m->R * pl.Npad);
+        ALLOC(m->d_C32, (size_t)n_r * m->KL);
+        ALLOC(m->d_IthT32, (size_t)m->T * n_theta);
+        ALLOC(m->d_Itc32, (size_t)m->T * n_theta);
+        ALLOC(m->d_colsum, pl.Npad);
+        m->tabB_chunk_bytes = (size_t)3 * pl.Npad * 32;
+        m->tabT_chunk_bytes = (size_t)3 * pl.NC * 32;
+        ALLOC(m->d_tabB, m->tabB_chunk_bytes * pl.n_kc);
+        ALLOC(m->d_tabT, m->tabT_chunk_bytes * pl.n_nc * (pl.Kpad / 16));
+    }
+#undef ALLOC
+    {
+        std::vector<double> edges;
+        edges.reserve(nedges);
+        edges.insert(edges.end(), r_edges, r_edges + n_r + 1);
+        edges.insert(edges.end(), theta_edges, theta_edges + n_theta + 1);
+        edges.insert(edges.end(), phi_edges, phi_edges + n_phi + 1);
+        st = cuda_status(cudaMemcpyAsync(m->d_r, edges.data(), nedges * sizeof(double), cudaMemcpyHostToDevice,
+                                         m->stream),
+                         "copy edges");
+        if (st != MP_OK) return fail(st);
+        st = cuda_status(cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream), "clear error word");
+        if (st != MP_OK) return fail(st);
+        st = cuda_status(launch_tables(m), "build tables");
+        if (st != MP_OK) return fail(st);
+        if (m->eff_prec != MP_PREC_FP64) {
+            st = cuda_status(launch_split_tables(m), "build split tables");
+            if (st != MP_OK) return fail(st);
+        }
+        st = cuda_status(cudaStreamSynchronize(m->stream), "table build");
+        if (st != MP_OK) return fail(st);
+    }
+    *out = m;
+    return MP_OK;
+}
+
+mp_status mp_mesh_destroy(mp_mesh *m)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard dg(m->device);
+    cudaStreamSynchronize(m->stream);
+    free_mesh_buffers(m);
+    delete m;
+    return MP_OK;
+}
+
+mp_status mp_mesh_set_stream(mp_mesh *m, void *cuda_stream)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard dg(m->device);
+    MP_TRY(cudaStreamSynchronize(m->stream));
+    if (m->profiling) prof_collect(m);
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    return MP_OK;
+}
+
+mp_status mp_mesh_get_info(const mp_mesh *m, mp_mesh_info *info)
+{
+    if (!m || !info) return set_error(MP_ERR_INVALID_ARG, "NULL argument");
+    info->n_r = m->n_r;
+    info->n_theta = m->n_t;
+    info->n_phi = m->n_p;
+    info->l_max = m->L;
+    info->n_moments = m->KL;
+    info->precision = m->prec;
+    info->effective_precision = m->eff_prec;
+    info->r_ref = m->r_ref;
+    info->G = m->G;
+    info->device_bytes = m->device_bytes;
+    return MP_OK;
+}
+
+mp_status mp_set_density(mp_mesh *m, const double *rho_dev)
+{
+    if (!m || !rho_dev) return set_error(MP_ERR_INVALID_ARG, "NULL argument");
+    m->rho = rho_dev;
+    return MP_OK;
+}
+
+mp_status mp_set_phi_output(mp_mesh *m, double *phi_dev)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    m->phi_user = phi_dev;
+    return MP_OK;
+}
+
+mp_status mp_solve(mp_mesh *m)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    if (!m->rho) return set_error(MP_ERR_NOT_READY, "no density bound (mp_set_density)");
+    DeviceGuard dg(m->device);
+    double *phi = m->phi_user;
+    if (!phi) {
+        mp_status st = ensure_phi_own(m);
+        if (st != MP_OK) return st;
+        phi = m->phi_own;
+    }
+    return run_solve(m, m->rho, phi);
+}
+
+mp_status mp_get_phi(mp_mesh *m, double *phi_dev)
+{
+    if (!m || !phi_dev) return set_error(MP_ERR_INVALID_ARG, "NULL argument");
+    if (!m->solved) return set_error(MP_ERR_NOT_READY, "no solve has run");
+    const double *src = m->phi_user ? m->phi_user : m->phi_own;
+    if (src == phi_dev) return MP_OK;
+    DeviceGuard dg(m->device);
+    MP_TRY(cudaMemcpyAsync(phi_dev, src, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    return MP_OK;
+}
+
+mp_status mp_get_moments(mp_mesh *m, double *ang_dev, double *mr_dev, double *mi_dev)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    if (!m->solved) return set_error(MP_ERR_NOT_READY, "no solve has run");
+    DeviceGuard dg(m->device);
+    const size_t a = (size_t)m->n_r * m->KL * sizeof(double), e = (size_t)(m->n_r + 1) * m->KL * sizeof(double);
+    if (ang_dev) MP_TRY(cudaMemcpyAsync(ang_dev, m->d_A, a, cudaMemcpyDeviceToDevice, m->stream));
+    if (mr_dev) MP_TRY(cudaMemcpyAsync(mr_dev, m->d_MR, e, cudaMemcpyDeviceToDevice, m->stream));
+    if (mi_dev) MP_TRY(cudaMemcpyAsync(mi_dev, m->d_MI, e, cudaMemcpyDeviceToDevice, m->stream));
+    return MP_OK;
+}
+
+mp_status mp_mesh_synchronize(mp_mesh *m)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard dg(m->device);
+    MP_TRY(cudaStreamSynchronize(m->stream));
+    int err = 0;
+    MP_TRY(cudaMemcpy(&err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        MP_TRY(cudaMemset(m->d_err, 0, sizeof(int)));
+        if (err & DEV_ERR_TIMEOUT) return set_error(MP_ERR_TIMEOUT, "a device-side pipeline wait ran out of time");
+        if (err & DEV_ERR_NONFINITE) return set_error(MP_ERR_NONFINITE, "density holds NaN or infinity");
+        return set_error(MP_ERR_CUDA, "device error word %d", err);
+    }
+    return MP_OK;
+}
+
+mp_status mp_solve_host(mp_mesh *m, const double *rho_host, double *phi_host)
+{
+    if (!m || !rho_host || !phi_host) return set_error(MP_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(m->device);
+    if (!m->rho_stage) {
+        mp_status st = dalloc(m, &m->rho_stage, (size_t)m->N);
+        if (st != MP_OK) return st;
+    }
+    mp_status st = ensure_phi_own(m);
+    if (st != MP_OK) return st;
+    const size_t bytes = (size_t)m->N * sizeof(double);
+    MP_TRY(cudaMemcpyAsync(m->rho_stage, rho_host, bytes, cudaMemcpyHostToDevice, m->stream));
+    st = run_solve(m, m->rho_stage, m->phi_own);
+    if (st != MP_OK) return st;
+    MP_TRY(cudaMemcpyAsync(phi_host, m->phi_own, bytes, cudaMemcpyDeviceToHost, m->stream));
+    return mp_mesh_synchronize(m);
+}
+
+mp_status mp_profile_enable(mp_mesh *m, int enable)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard dg(m->device);
+    cudaStreamSynchronize(m->stream);
+    prof_collect(m);
+    m->prof.clear();
+    m->profiling = enable ? 1 : 0;
+    return MP_OK;
+}
+
+mp_status mp_profile_read(mp_mesh *m, const char **names, int *launches, double *total_ms, int cap, int *n_out)
+{
+    if (!m || !n_out) return set_error(MP_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(m->device);
+    MP_TRY(cudaStreamSynchronize(m->stream));
+    prof_collect(m);
+    int n = 0;
+    for (auto &kv : m->prof) {
+        if (n < cap) {
+            if (names) names[n] = kv.second.name;
+            if (launches) launches[n] = kv.second.launches;
+            if (total_ms) total_ms[n] = kv.second.total_ms;
+        }
+        ++n;
+    }
+    *n_out = n;
+    return MP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+struct mp_batch {
+    std::vector<mp_mesh *> meshes;
+    std::vector<const void *> bound;  // rho / phi pointers the graph was captured with
+    cudaStream_t stream = nullptr;    // caller's stream (that of the first mesh)
+    cudaStream_t cap = nullptr;       // private stream the graph is captured on and runs on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int device = 0;
+};
+
+static void batch_bindings(const mp_batch *b, std::vector<const void *> &out)
+{
+    out.clear();
+    for (mp_mesh *m : b->meshes) {
+        out.push_back(m->rho);
+        out.push_back(m->phi_user ? m->phi_user : m->phi_own);
+    }
+}
+
+extern "C" {
+
+mp_status mp_batch_create(mp_mesh *const *meshes, int count, mp_batch **out)
+{
+    if (!meshes || count < 1 || !out) return set_error(MP_ERR_INVALID_ARG, "need count >= 1 meshes and out");
+    for (int i = 0; i < count; ++i)
+        if (!meshes[i]) return set_error(MP_ERR_INVALID_ARG, "mesh %d is NULL", i);
+    for (int i = 1; i < count; ++i)
+        if (meshes[i]->device != meshes[0]->device)
+            return set_error(MP_ERR_INVALID_ARG, "all meshes of a batch must live on one device");
+    mp_batch *b = new (std::nothrow) mp_batch();
+    if (!b) return set_error(MP_ERR_OOM, "host allocation failed");
+    b->meshes.assign(meshes, meshes + count);
+    b->stream = meshes[0]->stream;
+    b->device = meshes[0]->device;
+    DeviceGuard dg(b->device);
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        mp_status st = cuda_status(cudaGetLastError(), "batch stream/events");
+        if (b->cap) cudaStreamDestroy(b->cap);
+        if (b->ev_in) cudaEventDestroy(b->ev_in);
+        delete b;
+        return st == MP_OK ? set_error(MP_ERR_CUDA, "batch stream/events") : st;
+    }
+    *out = b;
+    return MP_OK;
+}
+
+mp_status mp_batch_solve(mp_batch *b)
+{
+    if (!b) return set_error(MP_ERR_INVALID_ARG, "batch is NULL");
+    DeviceGuard dg(b->device);
+    for (mp_mesh *m : b->meshes) {
+        if (!m->rho) return set_error(MP_ERR_NOT_READY, "a mesh of the batch has no density bound");
+        if (!m->phi_user) {
+            mp_status st = ensure_phi_own(m);
+            if (st != MP_OK) return st;
+        }
+    }
+    std::vector<const void *> now;
+    batch_bindings(b, now);
+    if (b->exec && now != b->bound) {
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+    }
+    if (!b->exec) {
+        // eager first pass (builds TMA descriptors), then capture the batch
+        std::vector<cudaStream_t> saved;
+        std::vector<int> prof;
+        for (mp_mesh *m : b->meshes) {
+            saved.push_back(m->stream);
+            prof.push_back(m->profiling);
+            m->stream = b->cap;
+            m->profiling = 0;
+        }
+        auto restore = [&] {
+            for (size_t i = 0; i < b->meshes.size(); ++i) {
+                b->meshes[i]->stream = saved[i];
+                b->meshes[i]->profiling = prof[i];
+            }
+        };
+        mp_status st = MP_OK;
+        cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+        cudaError_t e = cudaStreamBeginCapture(b->cap, mode);
+        if (e != cudaSuccess) {
+            restore();
+            return cuda_status(e, "cudaStreamBeginCapture");
+        }
+        for (mp_mesh *m : b->meshes) {
+            st = run_solve(m, m->rho, m->phi_user ? m->phi_user : m->phi_own);
+            if (st != MP_OK) break;
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(b->cap, &graph);
+        restore();
+        if (st != MP_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return cuda_status(e, "cudaGraphInstantiate");
+        }
+        b->graph = graph;
+        b->bound = now;
+    }
+    // order the replay after earlier work on the caller's stream, and later work after it
+    MP_TRY(cudaEventRecord(b->ev_in, b->stream));
+    MP_TRY(cudaStreamWaitEvent(b->cap, b->ev_in, 0));
+    MP_TRY(cudaGraphLaunch(b->exec, b->cap));
+    MP_TRY(cudaEventRecord(b->ev_out, b->cap));
+    MP_TRY(cudaStreamWaitEvent(b->stream, b->ev_out, 0));
+    return MP_OK;
+}
+
+mp_status mp_batch_destroy(mp_batch *b)
+{
+    if (!b) return set_error(MP_ERR_INVALID_ARG, "batch is NULL");
+    DeviceGuard dg(b->device);
+    cudaStreamSynchronize(b->stream);
+    cudaStreamSynchronize(b->cap);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaEventDestroy(b->ev_in);
+    cudaEventDestroy(b->ev_out);
+    cudaStreamDestroy(b->cap);
+    delete b;
+    return MP_OK;
+}
+
+// ---------------------------------------------------------------- tuner
+static std::string tune_key(const mp_mesh *m)
+{
+    std::ostringstream k;
+    k << m->n_r << ' ' << m->n_t << ' ' << m->n_p << ' ' << m->L << ' ' << m->eff_prec;
+    return k.str();
+}
+
+mp_status mp_autotune(mp_mesh *m, const char *cache_path)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    if (!m->rho) return set_error(MP_ERR_NOT_READY, "autotune needs a bound density");
+    DeviceGuard dg(m->device);
+    const std::string key = tune_key(m);
+    // cached choice?
+    if (cache_path) {
+        std::ifstream f(cache_path);
+        std::string line;
+        while (std::getline(f, line)) {
+            std::istringstream is(line);
+            int a, b, c, d, e, ns_s, ns_b, sw;
+            if (is >> a >> b >> c >> d >> e >> ns_s >> ns_b >> sw) {
+                std::ostringstream k;
+                k << a << ' ' << b << ' ' << c << ' ' << d << ' ' << e;
+                if (k.str() == key) {
+                    m->plan.ns_s = ns_s;
+                    m->plan.ns_b = ns_b;
+                    m->plan.scan_warps = sw;
+                    return MP_OK;
+                }
+            }
+        }
+    }
+    double *phi = m->phi_user;
+    if (!phi) {
+        mp_status st = ensure_phi_own(m);
+        if (st != MP_OK) return st;
+        phi = m->phi_own;
+    }
+    const SplitPlan base = m->plan;
+    struct Cand {
+        int ns_s, ns_b, sw;
+    };
+    std::vector<Cand> cands;
+    const int sws[] = {4, 8, 16, 32};
+    if (m->eff_prec == MP_PREC_FP64) {
+        for (int sw : sws) cands.push_back({base.ns_s, base.ns_b, sw});
+    } else {
+        for (int ns_s = 3; ns_s <= base.ns_s; ++ns_s)
+            for (int ns_b = 2; ns_b <= base.ns_b; ++ns_b)
+                for (int sw : sws) cands.push_back({ns_s, ns_b, sw});
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved_prof = m->profiling;
+    m->profiling = 0;
+    float best = FLT_MAX;
+    Cand best_c = {base.ns_s, base.ns_b, base.scan_warps};
+    mp_status st = MP_OK;
+    for (const Cand &c : cands) {
+        m->plan.ns_s = c.ns_s;
+        m->plan.ns_b = c.ns_b;
+        m->plan.scan_warps = c.sw;
+        st = run_solve(m, m->rho, phi);  // warm-up
+        if (st != MP_OK) break;
+        cudaEventRecord(e0, m->stream);
+        for (int it = 0; it < 3; ++it) {
+            st = run_solve(m, m->rho, phi);
+            if (st != MP_OK) break;
+        }
+        cudaEventRecord(e1, m->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = cuda_status(cudaGetLastError(), "autotune timing");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->profiling = saved_prof;
+    m->plan.ns_s = best_c.ns_s;
+    m->plan.ns_b = best_c.ns_b;
+    m->plan.scan_warps = best_c.sw;
+    if (st != MP_OK) {
+        m->plan = base;
+        return st;
+    }
+    if (cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        f << key << ' ' << best_c.ns_s << ' ' << best_c.ns_b << ' ' << best_c.sw << '\n';
+    }
+    return mp_mesh_synchronize(m);
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// mp_internal.h -- private state of a mesh and the launchers of every kernel.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <algorithm>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "multipole.h"
+#include "mp_errors.h"
+
+namespace mp {
+
+// Column p of a real moment: p(0,c) = 0, p(m,c) = 2m-1, p(m,s) = 2m.
+__host__ __device__ inline int pcol_m(int p) { return (p + 1) >> 1; }
+__host__ __device__ inline int tri(int l, int m) { return l * (l + 1) / 2 + m; }
+inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// Split-path geometry of one mesh (tcgen05 tensor-core contractions).
+struct SplitPlan {
+    int a_terms = 2;      // bf16 terms of the streaming operand (density deviation / G)
+    int n_products = 3;   // bf16 products accumulated per K step
+    int Npad = 0;         // projection GEMM N: 2L+1 rounded up to 16
+    int n_kc = 0;         // projection K chunks of 16 azimuthal cells
+    int Kpad = 0;         // synthesis GEMM K: 2L rounded up to 16 (m >= 1 columns)
+    int NC = 0;           // synthesis GEMM N per chunk: min(256, n_phi rounded to 16)
+    int n_nc = 0;         // synthesis N chunks
+    int proj_ctas = 0;    // persistent grid sizes
+    int synth_ctas = 0;
+    int proj_smem = 0;    // dynamic shared memory bytes
+    int synth_smem = 0;
+    int ns_s = 6;         // projection: TMA stages of the density
+    int ns_b = 3;         // synthesis: table stages
+    int scan_warps = 16;  // radial recurrences: warps (shell chunks) per block
+};
+
+struct ProfileEntry {
+    const char *name = nullptr;
+    int launches = 0;
+    double total_ms = 0.0;
+};
+
+}  // namespace mp
+
+struct mp_mesh {
+    int n_r = 0, n_t = 0, n_p = 0, L = 0;
+    int KL = 0, P = 0, T = 0;  // (L+1)^2, 2L+1, (L+1)(L+2)/2
+    long long R = 0;           // rows n_r * n_t
+    long long N = 0;           // cells
+    double G = 1.0, r_ref = 1.0;
+    int prec = 0, eff_prec = 0;
+    int origin = 0;            // r_edges[0] == 0
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    std::vector<double> h_r, h_th, h_ph;
+
+    // float64 tables
+    double *d_r = nullptr;
+    double *d_Ith = nullptr;   // [T][n_t]  int P~ sin dtheta over polar cells
+    double *d_dmu = nullptr;   // [n_t]
+    double *d_Iph = nullptr;   // [P][n_p]  int cos|sin(m phi) over azimuthal cells
+    double *d_Iphc = nullptr;  // [P][n_p]  Iph / dphi (cell mean)
+    double *d_WR = nullptr, *d_WI = nullptr;  // [L+1][n_r]
+    double *d_RR = nullptr, *d_RI = nullptr;  // [L+1][n_r]
+    double *d_V = nullptr;     // [n_r]
+
+    // moments (both paths)
+    double *d_A = nullptr;     // [n_r][KL]
+    double *d_MR = nullptr;    // [n_r+1][KL]
+    double *d_MI = nullptr;    // [n_r+1][KL]
+    double *d_C = nullptr;     // [n_r][KL]
+
+    // float64 path workspace
+    double *d_F64 = nullptr;   // [R][P]
+    double *d_G64 = nullptr;   // [R][P]
+
+    // split path tables and workspace
+    mp::SplitPlan plan;
+    float *d_F32 = nullptr;       // [R][Npad]
+    float *d_C32 = nullptr;       // [n_r][KL]
+    float *d_IthT32 = nullptr;    // [n_t][T]   Ith, transposed, float
+    float *d_Itc32 = nullptr;     // [T][n_t]   Ith / dmu, float
+    float *d_colsum = nullptr;    // [Npad]     sum_k Iph[p][k]
+    uint8_t *d_tabB = nullptr;    // projection B operand, bf16 x 3 terms, canonical layout
+    uint8_t *d_tabT = nullptr;    // synthesis B operand, bf16 x 3 terms, canonical layout
+    size_t tabB_chunk_bytes = 0, tabT_chunk_bytes = 0;
+
+    // bindings
+    const double *rho = nullptr;
+    double *phi_user = nullptr;
+    double *phi_own = nullptr;
+    double *rho_stage = nullptr;  // device copy target of mp_solve_host
+    int *d_err = nullptr;
+    int solved = 0;
+
+    // TMA descriptors, cached per bound pointer
+    CUtensorMap tm_rho{}, tm_phi{};
+    const void *tm_rho_ptr = nullptr, *tm_phi_ptr = nullptr;
+
+    // profiling
+    int profiling = 0;
+    std::vector<std::pair<const char *, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
+    std::map<std::string, mp::ProfileEntry> prof;
+    std::vector<cudaEvent_t> event_pool;
+
+    size_t device_bytes = 0;
+};
+
+namespace mp {
+
+// error detail of the calling host thread
+mp_status set_error(mp_status st, const char *fmt, ...);
+
+// ---- tables (float64, on the device) ----
+cudaError_t launch_tables(mp_mesh *m);
+cudaError_t launch_split_tables(mp_mesh *m);
+
+// ---- float64 path ----
+cudaError_t launch_fp64_project(mp_mesh *m, const double *rho);
+cudaError_t launch_fp64_theta(mp_mesh *m);
+cudaError_t launch_fp64_synth(mp_mesh *m, double *phi);
+
+// ---- shared radial recurrences ----
+cudaError_t launch_scan(mp_mesh *m, int want_f32);
+
+// ---- split path ----
+cudaError_t launch_split_project(mp_mesh *m, const double *rho);
+cudaError_t launch_split_theta(mp_mesh *m);
+cudaError_t launch_split_synth(mp_mesh *m, double *phi);
+int split_smem_limits(mp_mesh *m);  // 0 when the plan fits, else an error
+
+// profiling hooks used by the launchers
+void prof_begin(mp_mesh *m, const char *name, cudaEvent_t *ev_start);
+void prof_end(mp_mesh *m, const char *name, cudaEvent_t ev_start);
+
+}  // namespace mp

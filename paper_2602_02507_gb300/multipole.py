@@ -1,0 +1,264 @@
+"""Thin Python binding of the C ABI in include/multipole.h (libmultipole.so).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+PyTorch supplies device memory and streams.  Importing works without a GPU;
+using a mesh needs the compiled library and a CUDA device, and fails loudly
+otherwise (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmultipole.so")
+
+MP_OK = 0
+STATUS_NAMES = {
+    0: "MP_OK", 1: "MP_ERR_INVALID_ARG", 2: "MP_ERR_RANGE", 3: "MP_ERR_CUDA", 4: "MP_ERR_OOM",
+    5: "MP_ERR_NOT_READY", 6: "MP_ERR_NONFINITE", 7: "MP_ERR_TIMEOUT", 8: "MP_ERR_UNSUPPORTED",
+}
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16x6": 2}
+
+_lib = None
+
+
+class MultipoleError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{where}: {self.name}: {detail}")
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("l_max", ctypes.c_int), ("n_moments", ctypes.c_int), ("precision", ctypes.c_int),
+                ("effective_precision", ctypes.c_int), ("r_ref", ctypes.c_double), ("G", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmultipole.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    sigs = {
+        "mp_mesh_create": [dp, i, dp, i, dp, i, i, d, i, vp, ctypes.POINTER(vp)],
+        "mp_mesh_destroy": [vp],
+        "mp_mesh_set_stream": [vp, vp],
+        "mp_mesh_get_info": [vp, ctypes.POINTER(MeshInfo)],
+        "mp_set_density": [vp, vp],
+        "mp_set_phi_output": [vp, vp],
+        "mp_solve": [vp],
+        "mp_get_phi": [vp, vp],
+        "mp_get_moments": [vp, vp, vp, vp],
+        "mp_solve_host": [vp, vp, vp],
+        "mp_mesh_synchronize": [vp],
+        "mp_profile_enable": [vp, i],
+        "mp_profile_read": [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i), dp, i, ctypes.POINTER(i)],
+        "mp_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(vp)],
+        "mp_batch_solve": [vp],
+        "mp_batch_destroy": [vp],
+        "mp_autotune": [vp, ctypes.c_char_p],
+        "mp_last_error_detail": [ctypes.c_char_p, i],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.mp_status_string.argtypes = [i]
+    lib.mp_status_string.restype = ctypes.c_char_p
+    lib.mp_version.argtypes = []
+    lib.mp_version.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _detail(lib) -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib.mp_last_error_detail(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(status: int, where: str):
+    if status != MP_OK:
+        lib = load_library()
+        raise MultipoleError(status, where, _detail(lib))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _tensor_ptr(t, n: int, name: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Mesh:
+    """A spherical mesh with its device tables (mp_mesh_create)."""
+
+    def __init__(self, r_edges, theta_edges, phi_edges, l_max: int, G: float = 1.0,
+                 precision: str = "fp64", stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.r = np.ascontiguousarray(r_edges, dtype=np.float64)
+        self.theta = np.ascontiguousarray(theta_edges, dtype=np.float64)
+        self.phi = np.ascontiguousarray(phi_edges, dtype=np.float64)
+        self.shape = (self.r.size - 1, self.theta.size - 1, self.phi.size - 1)
+        self.l_max = int(l_max)
+        self.precision = precision
+        self._stream = stream
+        handle = ctypes.c_void_p()
+        st = lib.mp_mesh_create(_dptr(self.r), self.shape[0], _dptr(self.theta), self.shape[1],
+                                _dptr(self.phi), self.shape[2], self.l_max, float(G),
+                                PRECISIONS[precision], ctypes.c_void_p(_stream_handle(stream)),
+                                ctypes.byref(handle))
+        _check(st, "mp_mesh_create")
+        self._h = handle
+        self._rho = None
+        self._phi = None
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mp_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def cells(self) -> int:
+        n_r, n_t, n_p = self.shape
+        return n_r * n_t * n_p
+
+    @property
+    def n_moments(self) -> int:
+        return (self.l_max + 1) ** 2
+
+    def info(self) -> dict:
+        inf = MeshInfo()
+        _check(self._lib.mp_mesh_get_info(self._h, ctypes.byref(inf)), "mp_mesh_get_info")
+        return {f: getattr(inf, f) for f, _ in MeshInfo._fields_}
+
+    def set_stream(self, stream):
+        _check(self._lib.mp_mesh_set_stream(self._h, ctypes.c_void_p(_stream_handle(stream))), "mp_mesh_set_stream")
+
+    # -- bindings and solve
+    def set_density(self, rho):
+        _check(self._lib.mp_set_density(self._h, ctypes.c_void_p(_tensor_ptr(rho, self.cells, "rho"))),
+               "mp_set_density")
+        self._rho = rho
+
+    def set_phi_output(self, phi):
+        ptr = None if phi is None else _tensor_ptr(phi, self.cells, "phi")
+        _check(self._lib.mp_set_phi_output(self._h, ctypes.c_void_p(ptr)), "mp_set_phi_output")
+        self._phi = phi
+
+    def solve(self):
+        _check(self._lib.mp_solve(self._h), "mp_solve")
+
+    def get_phi(self, out):
+        _check(self._lib.mp_get_phi(self._h, ctypes.c_void_p(_tensor_ptr(out, self.cells, "out"))), "mp_get_phi")
+        return out
+
+    def get_moments(self, ang=None, mr=None, mi=None):
+        n_r, K = self.shape[0], self.n_moments
+        p = [None if t is None else ctypes.c_void_p(_tensor_ptr(t, s, nm))
+             for t, s, nm in ((ang, n_r * K, "ang"), (mr, (n_r + 1) * K, "mr"), (mi, (n_r + 1) * K, "mi"))]
+        _check(self._lib.mp_get_moments(self._h, *p), "mp_get_moments")
+
+    def synchronize(self):
+        _check(self._lib.mp_mesh_synchronize(self._h), "mp_mesh_synchronize")
+
+    def solve_host(self, rho_host: np.ndarray, phi_host: np.ndarray):
+        """End-to-end solve from host arrays (float64, rho layout; pinned is fastest)."""
+        for a, nm in ((rho_host, "rho_host"), (phi_host, "phi_host")):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != self.cells:
+                raise ValueError(f"{nm} must be a contiguous float64 array of {self.cells} values")
+        _check(self._lib.mp_solve_host(self._h, ctypes.c_void_p(rho_host.ctypes.data),
+                                       ctypes.c_void_p(phi_host.ctypes.data)), "mp_solve_host")
+
+    def solve_host_ptr(self, rho_ptr: int, phi_ptr: int):
+        """End-to-end solve from host addresses (e.g. pinned torch tensors)."""
+        _check(self._lib.mp_solve_host(self._h, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(phi_ptr)),
+               "mp_solve_host")
+
+    # -- per-kernel timing
+    def profile(self, enable: bool = True):
+        _check(self._lib.mp_profile_enable(self._h, int(enable)), "mp_profile_enable")
+
+    def profile_read(self) -> dict:
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        launches = (ctypes.c_int * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = ctypes.c_int(0)
+        _check(self._lib.mp_profile_read(self._h, names, launches, ms, cap, ctypes.byref(n)), "mp_profile_read")
+        return {names[k].decode(): {"launches": launches[k], "total_ms": ms[k]} for k in range(min(cap, n.value))}
+
+    def autotune(self, cache_path: str | None = None):
+        _check(self._lib.mp_autotune(self._h, cache_path.encode() if cache_path else None), "mp_autotune")
+
+
+class Batch:
+    """Several meshes solved together as one captured CUDA graph (mp_batch_*)."""
+
+    def __init__(self, meshes):
+        lib = load_library()
+        self._lib = lib
+        self.meshes = list(meshes)
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
+        h = ctypes.c_void_p()
+        _check(lib.mp_batch_create(arr, len(self.meshes), ctypes.byref(h)), "mp_batch_create")
+        self._h = h
+
+    def solve(self):
+        _check(self._lib.mp_batch_solve(self._h), "mp_batch_solve")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def status_string(code: int) -> str:
+    return load_library().mp_status_string(code).decode()
+
+
+def version() -> int:
+    return load_library().mp_version()

@@ -1,0 +1,125 @@
+"""C-ABI behaviour on the GPU: error reporting, host end-to-end, batches, profiling, tuner."""
+import numpy as np
+import pytest
+
+from gpu_helpers import gpu_solve, oracle_solve, phi_rel_err
+from paper_2602_02507_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_nonfinite_density_is_reported(prec):
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = W.presn(n_r=8, n_theta=16, n_phi=32, L=4)
+    m = w.mesh
+    rho = torch.from_numpy(w.rho).cuda()
+    rho.view(-1)[1234] = float("nan")
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=prec) as mesh:
+        mesh.set_density(rho)
+        mesh.solve()
+        with pytest.raises(mpl.MultipoleError) as ei:
+            mesh.synchronize()
+        assert ei.value.name == "MP_ERR_NONFINITE"
+        mesh.synchronize()  # the error word was cleared
+
+
+def test_solve_without_density_is_not_ready():
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = W.presn(n_r=4, n_theta=8, n_phi=16, L=2, materialize=False)
+    m = w.mesh
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G) as mesh:
+        with pytest.raises(mpl.MultipoleError) as ei:
+            mesh.solve()
+        assert ei.value.name == "MP_ERR_NOT_READY"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_host_end_to_end_equals_device_solve(prec):
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = W.presn(n_r=32, n_theta=32, n_phi=64, L=8)
+    m = w.mesh
+    dev = gpu_solve(w, prec, want_moments=False)["phi"]
+    rho_h = torch.from_numpy(w.rho).pin_memory()
+    phi_h = torch.empty_like(rho_h).pin_memory()
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=prec) as mesh:
+        mesh.solve_host_ptr(rho_h.data_ptr(), phi_h.data_ptr())
+    assert np.array_equal(phi_h.numpy(), dev)
+
+
+def test_batch_equals_individual_solves():
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    ws = [W.presn(n_r=16, n_theta=32, n_phi=64, L=8, seed=11),
+          W.presn(n_r=24, n_theta=16, n_phi=32, L=4, seed=12),
+          W.random_small((6, 8, 9), 3, seed=13, r0=0.0, r1=1.0)]
+    precs = ["bf16x3", "fp64", "fp64"]
+    meshes, outs = [], []
+    for w, p in zip(ws, precs):
+        m = w.mesh
+        mesh = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=p)
+        rho = torch.from_numpy(w.rho).cuda()
+        phi = torch.zeros_like(rho)
+        mesh.set_density(rho)
+        mesh.set_phi_output(phi)
+        meshes.append(mesh)
+        outs.append((rho, phi))
+    b = mpl.Batch(meshes)
+    for _ in range(2):
+        b.solve()
+    meshes[0].synchronize()
+    for w, p, (rho, phi) in zip(ws, precs, outs):
+        ref = gpu_solve(w, p, want_moments=False)["phi"]
+        assert np.array_equal(phi.cpu().numpy(), ref)
+    b.close()
+    for mesh in meshes:
+        mesh.close()
+
+
+def test_profile_names_every_kernel():
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = W.presn(n_r=16, n_theta=32, n_phi=64, L=8)
+    m = w.mesh
+    rho = torch.from_numpy(w.rho).cuda()
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3") as mesh:
+        mesh.set_density(rho)
+        mesh.profile(True)
+        for _ in range(3):
+            mesh.solve()
+        prof = mesh.profile_read()
+    assert set(prof) == {"split_phi_project_tc", "split_theta_contract", "radial_scan", "split_synth_tc"}
+    assert all(v["launches"] == 3 and v["total_ms"] > 0 for v in prof.values())
+
+
+def test_autotune_keeps_results(tmp_path):
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = W.presn(n_r=32, n_theta=32, n_phi=64, L=8)
+    m = w.mesh
+    ref = oracle_solve(w)["phi"]
+    rho = torch.from_numpy(w.rho).cuda()
+    phi = torch.empty_like(rho)
+    cache = str(tmp_path / "tune.txt")
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3") as mesh:
+        mesh.set_density(rho)
+        mesh.set_phi_output(phi)
+        mesh.autotune(cache)
+        mesh.solve()
+        mesh.synchronize()
+        assert phi_rel_err(phi.cpu().numpy(), ref) <= 1e-6
+    assert open(cache).read().strip()
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3") as mesh2:
+        mesh2.set_density(rho)
+        mesh2.autotune(cache)  # served from the cache

@@ -1,0 +1,104 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+float64 path: Phi within 1e-12 (pointwise relative), moments within 1e-12 per degree.
+split-precision paths: Phi within 1e-6 (pointwise relative).
+
+Meshes keep shells moderately thin: the midpoint split of Eq. (Solution) weighs a
+shell's own degree-l moment by about (r_{i+1}/r_i)^l, so on meshes with a few
+shells per decade any rounding difference in high-degree moments is amplified
+by that factor (the float64 path and the oracle then differ beyond 1e-12 for
+reasons of conditioning, not of arithmetic).
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import gpu_solve, oracle_solve, per_l_errors, phi_rel_err, significant_degrees
+from paper_2602_02507_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _axisym():
+    w = W.random_small((6, 10, 1), 6, seed=4, r0=0.0, r1=1.0)
+    return w
+
+
+def _one_polar_cell():
+    return W.random_small((6, 1, 12), 5, seed=5, r0=0.1, r1=1.0)
+
+
+FP64_CASES = {
+    "spheroid_64x32x64_L8": lambda: W.spheroid(),
+    "ragged_7x19x37_L5_origin": lambda: W.random_small((7, 19, 37), 5, seed=1, r0=0.0, r1=2.0, uneven=True),
+    "geometric_9x23x40_L9": lambda: W.random_small((9, 23, 40), 9, seed=2, r0=1e5, r1=1e9, geometric=True,
+                                                   uneven=True),
+    "monopole_L0": lambda: W.random_small((5, 8, 16), 0, seed=3),
+    "axisymmetric_nphi1": _axisym,
+    "one_polar_cell": _one_polar_cell,
+    "presn_64x32x64_L16": lambda: W.presn(n_r=64, n_theta=32, n_phi=64, L=16),
+}
+
+
+@pytest.mark.parametrize("name", list(FP64_CASES))
+def test_fp64_path_matches_oracle(name):
+    w = FP64_CASES[name]()
+    ref = oracle_solve(w)
+    got = gpu_solve(w, "fp64")
+    assert got["info"]["effective_precision"] == 0
+    assert phi_rel_err(got["phi"], ref["phi"]) <= 1e-12
+    L = w.mesh.L
+    assert max(per_l_errors(got["A"], ref["A"], L)) <= 1e-12
+    # edge moments scale differently per degree: compare each significant degree on its own
+    for key in ("MR", "MI"):
+        errs = per_l_errors(got[key], ref[key], L, floor=0.0)
+        for l in significant_degrees(ref["A"], L):
+            assert errs[l] <= 1e-12, (key, l, errs[l])
+
+
+SPLIT_CASES = {
+    "spheroid_64x32x64_L8": (lambda: W.spheroid(), ("bf16x3", "bf16x6")),
+    "presn_64x32x64_L16": (lambda: W.presn(n_r=64, n_theta=32, n_phi=64, L=16), ("bf16x3", "bf16x6")),
+    "ragged_rows_5x27x48_L7": (lambda: W.presn(n_r=5, n_theta=27, n_phi=48, L=7, r_lo=1e7, r_hi=2e7),
+                               ("bf16x3", "bf16x6")),
+    "two_phi_chunks_3x48x320_L6": (lambda: W.presn(n_r=3, n_theta=48, n_phi=320, L=6, r_lo=1e7, r_hi=1.5e7),
+                                   ("bf16x3", "bf16x6")),
+    "monopole_L0_8x16x32": (lambda: W.presn(n_r=8, n_theta=16, n_phi=32, L=0), ("bf16x3",)),
+    "random_rough_6x32x64_L8": (lambda: W.random_small((6, 32, 64), 8, seed=8, r0=0.2, r1=1.0), ("bf16x6",)),
+}
+
+
+@pytest.mark.parametrize("name,prec", [(n, p) for n, (_, ps) in SPLIT_CASES.items() for p in ps])
+def test_split_path_matches_oracle(name, prec):
+    w = SPLIT_CASES[name][0]()
+    ref = oracle_solve(w)
+    got = gpu_solve(w, prec)
+    assert got["info"]["effective_precision"] == {"bf16x3": 1, "bf16x6": 2}[prec]
+    err = phi_rel_err(got["phi"], ref["phi"])
+    assert err <= 1e-6, err
+    # monopole moment and edge moments carry float32-level accuracy
+    assert per_l_errors(got["A"], ref["A"], w.mesh.L)[0] <= 1e-6
+
+
+def test_presn_full_size_split_and_fp64():
+    """512 x 128 x 256 cells, L = 16: every cell against the oracle, both paths."""
+    w = W.presn()
+    ref = oracle_solve(w)
+    for prec, tol in (("bf16x3", 1e-6), ("fp64", 1e-12)):
+        got = gpu_solve(w, prec, want_moments=False)
+        assert phi_rel_err(got["phi"], ref["phi"]) <= tol, prec
+
+
+def test_split_falls_back_to_fp64_for_odd_nphi():
+    w = W.random_small((6, 24, 37), 4, seed=6, r0=0.0, r1=1.0)
+    got = gpu_solve(w, "bf16x3")
+    assert got["info"]["effective_precision"] == 0
+    assert phi_rel_err(got["phi"], oracle_solve(w)["phi"]) <= 1e-12
