@@ -329,6 +329,8 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_err = float(np.max(np.abs(phi_h.numpy() - p_split)))
 
+    rates = mpl.probe_rates()
+
     # ---- roofline of the dominant kernel
     log("kernels:", json.dumps(prof))
     dom = max(prof, key=lambda k: prof[k]["total_ms"])
@@ -363,6 +365,8 @@ def run_ours(args):
             "e2e": {"value": world * ke / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * cells,
                     "d2h_bytes_per_step": 8 * cells, "steps": ke, "max_abs_diff_vs_device_solve": e2e_err},
             "gpu_launches": 4 * args.steps,
+            "device_rates": {"fp64_tflops_measured": rates["fp64_tflops"],
+                             "cvt_f64_to_f32_per_s_measured": rates["cvt_f64_f32_per_s"]},
             "clocks": clk,
         }
         if cpu is not None:

@@ -204,6 +204,14 @@ MP_API mp_status mp_batch_destroy(mp_batch *batch);
  */
 MP_API mp_status mp_autotune(mp_mesh *mesh, const char *cache_path);
 
+/*
+ * Device rate probes (diagnostics, not part of a solve): measures, on the
+ * current device, the float64 FMA rate in TFLOP/s (the roofline of the float64
+ * path) and the hardware float64 -> float32 conversion rate in conversions/s.
+ * Allocates 16 bytes of device memory for the duration of the call.
+ */
+MP_API mp_status mp_probe_rates(double *fp64_tflops, double *cvt_f64_f32_per_s);
+
 /* Static description of a status code. */
 MP_API const char *mp_status_string(mp_status status);
 

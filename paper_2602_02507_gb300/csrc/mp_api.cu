@@ -219,7 +219,7 @@ static mp_status plan_split(mp_mesh *m)
     pl.a_terms = (m->prec == MP_PREC_BF16X6) ? 3 : 2;
     pl.n_products = (m->prec == MP_PREC_BF16X6) ? 6 : 3;
     pl.Npad = round_up(m->P, 16);
-    pl.n_kc = (m->n_p + 15) / 16;
+    pl.n_kc = (m->n_p + 31) / 32;
     pl.Kpad = std::max(16, round_up(2 * m->L, 16));
     pl.NC = std::min(256, round_up(m->n_p, 16));
     pl.n_nc = (m->n_p + pl.NC - 1) / pl.NC;
@@ -366,7 +366,7 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
         ALLOC(m->d_IthT32, (size_t)m->T * n_theta);
         ALLOC(m->d_Itc32, (size_t)m->T * n_theta);
         ALLOC(m->d_colsum, pl.Npad);
-        m->tabB_chunk_bytes = (size_t)3 * pl.Npad * 32;
+        m->tabB_chunk_bytes = (size_t)3 * pl.Npad * 64;
         m->tabT_chunk_bytes = (size_t)3 * pl.NC * 32;
         ALLOC(m->d_tabB, m->tabB_chunk_bytes * pl.n_kc);
         ALLOC(m->d_tabT, m->tabT_chunk_bytes * pl.n_nc * (pl.Kpad / 16));

@@ -36,6 +36,7 @@ struct SplitPlan {
     int synth_smem = 0;
     int ns_s = 6;         // projection: TMA stages of the density
     int ns_b = 3;         // synthesis: table stages
+    int jblock = 0;       // synthesis: tiles of (shells x 32 polar cells) with a resident table slice
     int scan_warps = 16;  // radial recurrences: warps (shell chunks) per block
 };
 

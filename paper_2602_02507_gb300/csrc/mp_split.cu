@@ -54,18 +54,33 @@ __device__ __forceinline__ bool warp_all(bool v) { return __all_sync(kFull, v); 
 // (a1) phi projection
 // ----------------------------------------------------------------------------
 namespace proj {
-constexpr int BK = 16;                  // float64 columns per TMA tile (128 bytes)
-constexpr int S_BYTES = kBM * BK * 8;   // 16 KB
-constexpr int A_TERM_BYTES = kBM * BK * 2;
+constexpr int BK = 32;                       // float64 cells per stage (two TMA boxes of 16)
+constexpr int BOX_BYTES = kBM * 16 * 8;      // one [128 x 16] float64 box, 16 KB
+constexpr int S_BYTES = 2 * BOX_BYTES;       // 32 KB
+constexpr int A_TERM_BYTES = kBM * BK * 2;   // [128 x 32] bf16, 8 KB
+constexpr int SBO = (BK / 8) * 128;          // 8-row group stride of A and B chunks
 }  // namespace proj
 
+// Position in a ring of mbarrier-guarded stages: index and phase advance together.
+struct Ring {
+    int idx = 0;
+    uint32_t phase = 0;
+    __device__ __forceinline__ void next(int n)
+    {
+        if (++idx == n) {
+            idx = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
 struct ProjParams {
-    const uint8_t *tabB;   // [n_kc][3][Npad x 16] bf16, canonical layout
+    const uint8_t *tabB;   // [n_kc][3][Npad x 32] bf16, canonical layout
     const float *colsum;   // [Npad]
     float *F;              // [R][Npad]
     int *err;
     long long R;
-    int n_kc, Npad, n_tiles, ns_s, ns_o;
+    int n_p, n_kc, Npad, n_tiles, ns_s, ns_o;
     uint32_t bchunk;       // bytes of one B chunk (3 terms)
 };
 
@@ -81,7 +96,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
     uint8_t *sA = sB + (size_t)NS_S * prm.bchunk;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sA + (size_t)NS_O * A_TERMS * A_TERM_BYTES);
     uint64_t *s_full = bars, *s_empty = bars + NS_S;
-    uint64_t *o_full = bars + 2 * NS_S, *o_empty = o_full + NS_O;
+    uint64_t *b_full = bars + 2 * NS_S, *b_empty = b_full + NS_S;
+    uint64_t *o_full = bars + 4 * NS_S, *o_empty = o_full + NS_O;
     uint64_t *acc_full = o_empty + NS_O, *acc_empty = acc_full + 2, *drain = acc_empty + 2;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
@@ -94,7 +110,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS_S; ++s) {
             mbar_init(smem_u32(&s_full[s]), 1);
-            mbar_init(smem_u32(&s_empty[s]), kConvWarps + 1);
+            mbar_init(smem_u32(&s_empty[s]), kConvWarps);  // density stages: free once converted
+            mbar_init(smem_u32(&b_full[s]), 1);
+            mbar_init(smem_u32(&b_empty[s]), 1);           // table stages: free once the MMAs read them
         }
         for (int o = 0; o < NS_O; ++o) {
             mbar_init(smem_u32(&o_full[o]), kConvWarps);
@@ -118,31 +136,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
     const uint32_t tmem_base = *tmem_holder;
 
     if (warp == 0) {
-        // ---------------- producer: TMA tile of rho + bulk copy of the table chunk
+        // ---------------- producer: two TMA boxes of rho, and the table chunk on its own ring
         if (lane == 0) {
             tma_prefetch_desc(&tmS);
-            uint32_t g = 0;
-            long long last_g = -1;
+            Ring rs;
+            int issued = 0;
             for (int tile = blockIdx.x; tile < prm.n_tiles && !*abort_flag; tile += gridDim.x) {
-                for (int kc = 0; kc < prm.n_kc; ++kc, ++g) {
-                    const int s = g % NS_S;
-                    const uint32_t ph = (g / NS_S) & 1;
-                    if (!mbar_wait(smem_u32(&s_empty[s]), ph ^ 1, abort_flag, prm.err)) break;
-                    const uint32_t fb = smem_u32(&s_full[s]);
-                    mbar_arrive_expect_tx(fb, S_BYTES + prm.bchunk);
-                    tma_load_2d(smem_u32(sS + (size_t)s * S_BYTES), &tmS, fb, kc * BK, tile * kBM);
-                    bulk_load(smem_u32(sB + (size_t)s * prm.bchunk), prm.tabB + (size_t)kc * prm.bchunk, prm.bchunk,
-                              fb);
-                    last_g = g;
+                for (int kc = 0; kc < prm.n_kc; ++kc, rs.next(NS_S)) {
+                    if (!mbar_wait(smem_u32(&s_empty[rs.idx]), rs.phase ^ 1, abort_flag, prm.err)) break;
+                    const uint32_t fb = smem_u32(&s_full[rs.idx]);
+                    const bool two = kc * BK + 16 < prm.n_p;  // the second box holds cells
+                    mbar_arrive_expect_tx(fb, two ? S_BYTES : BOX_BYTES);
+                    const uint32_t dst = smem_u32(sS + (size_t)rs.idx * S_BYTES);
+                    tma_load_2d(dst, &tmS, fb, kc * BK, tile * kBM);
+                    if (two) tma_load_2d(dst + BOX_BYTES, &tmS, fb, kc * BK + 16, tile * kBM);
+                    if (!mbar_wait(smem_u32(&b_empty[rs.idx]), rs.phase ^ 1, abort_flag, prm.err)) {
+                        ++issued;
+                        break;
+                    }
+                    const uint32_t bb = smem_u32(&b_full[rs.idx]);
+                    mbar_arrive_expect_tx(bb, prm.bchunk);
+                    bulk_load(smem_u32(sB + (size_t)rs.idx * prm.bchunk), prm.tabB + (size_t)kc * prm.bchunk,
+                              prm.bchunk, bb);
+                    ++issued;
                 }
             }
-            if (*abort_flag && last_g >= 0) {
+            if (*abort_flag && issued > 0) {
                 // drain copies still in flight into this CTA's shared memory
-                for (long long gg = last_g; gg >= 0 && gg > last_g - NS_S; --gg) {
-                    const int s = (int)(gg % NS_S);
-                    const uint32_t ph = (uint32_t)((gg / NS_S) & 1);
+                Ring back = rs;
+                for (int n = 0; n < NS_S && n < issued; ++n) {
+                    back.idx = (back.idx == 0) ? NS_S - 1 : back.idx - 1;
+                    if (back.idx == NS_S - 1) back.phase ^= 1u;
                     const long long t0 = clock64();
-                    while (!mbar_try_wait(smem_u32(&s_full[s]), ph) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
+                    while ((!mbar_try_wait(smem_u32(&s_full[back.idx]), back.phase) ||
+                            !mbar_try_wait(smem_u32(&b_full[back.idx]), back.phase)) &&
+                           clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
                     }
                 }
             }
@@ -151,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(kBM, Npad);
-            uint32_t g = 0;
+            Ring rs, ro;
             int lt = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ++lt) {
@@ -160,21 +188,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)b * acc_stride;
-                for (int kc = 0; kc < prm.n_kc; ++kc, ++g) {
-                    const int s = g % NS_S, o = g % NS_O;
-                    ok = mbar_wait(smem_u32(&o_full[o]), (g / NS_O) & 1, abort_flag, prm.err);
+                for (int kc = 0; kc < prm.n_kc; ++kc, rs.next(NS_S), ro.next(NS_O)) {
+                    ok = mbar_wait(smem_u32(&o_full[ro.idx]), ro.phase, abort_flag, prm.err) &&
+                         mbar_wait(smem_u32(&b_full[rs.idx]), rs.phase, abort_flag, prm.err);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t a_base = smem_u32(sA + (size_t)o * A_TERMS * A_TERM_BYTES);
-                    const uint32_t b_base = smem_u32(sB + (size_t)s * prm.bchunk);
+                    const uint32_t a_base = smem_u32(sA + (size_t)ro.idx * A_TERMS * A_TERM_BYTES);
+                    const uint32_t b_base = smem_u32(sB + (size_t)rs.idx * prm.bchunk);
 #pragma unroll
-                    for (int pi = 0; pi < NPROD; ++pi) {
-                        const uint64_t ad = sdesc_noswizzle(a_base + c_prod_a[pi] * A_TERM_BYTES, 128, 256);
-                        const uint64_t bd = sdesc_noswizzle(b_base + c_prod_b[pi] * Npad * 32, 128, 256);
-                        umma_bf16(d_tmem, ad, bd, idesc, (kc | pi) != 0);
+                    for (int ks = 0; ks < BK / 16; ++ks) {
+#pragma unroll
+                        for (int pi = 0; pi < NPROD; ++pi) {
+                            const uint64_t ad =
+                                sdesc_noswizzle(a_base + c_prod_a[pi] * A_TERM_BYTES + ks * 256, 128, SBO);
+                            const uint64_t bd =
+                                sdesc_noswizzle(b_base + c_prod_b[pi] * Npad * (BK * 2) + ks * 256, 128, SBO);
+                            umma_bf16(d_tmem, ad, bd, idesc, (kc | ks | pi) != 0);
+                        }
                     }
-                    umma_commit(smem_u32(&o_empty[o]));
-                    umma_commit(smem_u32(&s_empty[s]));
+                    umma_commit(smem_u32(&o_empty[ro.idx]));
+                    umma_commit(smem_u32(&b_empty[rs.idx]));
                 }
                 if (!ok) break;
                 umma_commit(smem_u32(&acc_full[b]));
@@ -189,10 +222,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
         const int cw = warp - 2, qd = warp & 3, half = cw >> 2;
         const int row = qd * 32 + lane;
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
-        uint32_t g = 0;
+        Ring rs, ro;
         int lt = 0, prev_tile = -1;
         float sref = 0.0f, sref_prev = 0.0f;
-        bool bad = false, ok = true;
+        uint32_t efmax = 0;  // largest float64 exponent field seen (flags values beyond float32)
+        bool ok = true;
 
         auto epilogue = [&](int etile, int elt, float sr) -> bool {
             const int b = elt & 1;
@@ -209,14 +243,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
                     const float4 c0 = *reinterpret_cast<const float4 *>(prm.colsum + cg * 8);
                     const float4 c1 = *reinterpret_cast<const float4 *>(prm.colsum + cg * 8 + 4);
                     float4 o0, o1;
-                    o0.x = __uint_as_float(v[0]) + sr * c0.x;
-                    o0.y = __uint_as_float(v[1]) + sr * c0.y;
-                    o0.z = __uint_as_float(v[2]) + sr * c0.z;
-                    o0.w = __uint_as_float(v[3]) + sr * c0.w;
-                    o1.x = __uint_as_float(v[4]) + sr * c1.x;
-                    o1.y = __uint_as_float(v[5]) + sr * c1.y;
-                    o1.z = __uint_as_float(v[6]) + sr * c1.z;
-                    o1.w = __uint_as_float(v[7]) + sr * c1.w;
+                    o0.x = fmaf(sr, c0.x, __uint_as_float(v[0]));
+                    o0.y = fmaf(sr, c0.y, __uint_as_float(v[1]));
+                    o0.z = fmaf(sr, c0.z, __uint_as_float(v[2]));
+                    o0.w = fmaf(sr, c0.w, __uint_as_float(v[3]));
+                    o1.x = fmaf(sr, c1.x, __uint_as_float(v[4]));
+                    o1.y = fmaf(sr, c1.y, __uint_as_float(v[5]));
+                    o1.z = fmaf(sr, c1.z, __uint_as_float(v[6]));
+                    o1.w = fmaf(sr, c1.w, __uint_as_float(v[7]));
                     float4 *dst = reinterpret_cast<float4 *>(prm.F + grow * Npad + cg * 8);
                     dst[0] = o0;
                     dst[1] = o1;
@@ -228,43 +262,63 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
             return true;
         };
 
+        // this thread converts cells [16 half, 16 half + 16) of every stage: box `half`
         for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ++lt) {
-            for (int kc = 0; kc < prm.n_kc; ++kc, ++g) {
-                const int s = g % NS_S, o = g % NS_O;
-                ok = warp_all(mbar_wait(smem_u32(&s_full[s]), (g / NS_S) & 1, abort_flag, prm.err));
+            for (int kc = 0; kc < prm.n_kc; ++kc, rs.next(NS_S), ro.next(NS_O)) {
+                ok = warp_all(mbar_wait(smem_u32(&s_full[rs.idx]), rs.phase, abort_flag, prm.err));
                 if (!ok) break;
-                ok = warp_all(mbar_wait(smem_u32(&o_empty[o]), ((g / NS_O) & 1) ^ 1, abort_flag, prm.err));
+                ok = warp_all(mbar_wait(smem_u32(&o_empty[ro.idx]), ro.phase ^ 1, abort_flag, prm.err));
                 if (!ok) break;
-                const uint8_t *srow = sS + (size_t)s * S_BYTES + row * 128;
+                const uint8_t *sbox = sS + (size_t)rs.idx * S_BYTES + row * 128;
                 if (kc == 0) {
-                    const uint2 v0 = *reinterpret_cast<const uint2 *>(srow + ((row & 7) << 4));
-                    sref = f64w_to_f32(v0.x, v0.y);
+                    const uint2 v0 = *reinterpret_cast<const uint2 *>(sbox + ((row & 7) << 4));
+                    uint32_t e0;
+                    sref = f64w_to_f32_fast(v0.x, v0.y, e0);
                 }
-                uint32_t w0[4], w1[4], w2[4];
+                const uint8_t *srow = sbox + half * BOX_BYTES;
+                const int kfirst = kc * BK + half * 16;           // first cell of this thread's box
+                const bool full = kfirst + 16 <= prm.n_p;         // warp-uniform
+                uint32_t w0[8], w1[8], w2[8];
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const int c = half * 4 + cc;
+                for (int c = 0; c < 8; ++c) {
                     const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((c ^ (row & 7)) << 4));
-                    bad |= f64w_nonfinite(v.y) | f64w_nonfinite(v.w);
-                    const float x0 = f64w_to_f32(v.x, v.y) - sref;
-                    const float x1 = f64w_to_f32(v.z, v.w) - sref;
+                    uint32_t e0, e1;
+                    float x0 = f64w_to_f32_fast(v.x, v.y, e0) - sref;
+                    float x1 = f64w_to_f32_fast(v.z, v.w, e1) - sref;
+                    if (!full) {
+                        // cells past the last azimuthal cell hold no data: zero deviation
+                        const bool in0 = kfirst + 2 * c < prm.n_p, in1 = kfirst + 2 * c + 1 < prm.n_p;
+                        x0 = in0 ? x0 : 0.0f;
+                        x1 = in1 ? x1 : 0.0f;
+                        e0 = in0 ? e0 : 0u;
+                        e1 = in1 ? e1 : 0u;
+                    }
+                    efmax = max(efmax, max(e0, e1));
                     const uint32_t t0 = pack_bf16x2(x0, x1);
                     const float r0 = x0 - bf16lo_to_f32(t0), r1 = x1 - bf16hi_to_f32(t0);
                     const uint32_t t1 = pack_bf16x2(r0, r1);
-                    w0[cc] = t0;
-                    w1[cc] = t1;
-                    if (A_TERMS == 3) w2[cc] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
+                    w0[c] = t0;
+                    w1[c] = t1;
+                    if (A_TERMS == 3) w2[c] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
                 }
-                uint8_t *adst = sA + (size_t)o * A_TERMS * A_TERM_BYTES + (row >> 3) * 256 + half * 128 + (row & 7) * 16;
-                *reinterpret_cast<uint4 *>(adst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                *reinterpret_cast<uint4 *>(adst + A_TERM_BYTES) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                if (A_TERMS == 3)
-                    *reinterpret_cast<uint4 *>(adst + 2 * A_TERM_BYTES) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+                // K groups 2 half and 2 half + 1 of the [128 x 32] A tile, each term
+                uint8_t *adst = sA + (size_t)ro.idx * A_TERMS * A_TERM_BYTES + (row >> 3) * SBO + half * 256 +
+                                (row & 7) * 16;
+#pragma unroll
+                for (int kg = 0; kg < 2; ++kg) {
+                    *reinterpret_cast<uint4 *>(adst + kg * 128) =
+                        make_uint4(w0[4 * kg], w0[4 * kg + 1], w0[4 * kg + 2], w0[4 * kg + 3]);
+                    *reinterpret_cast<uint4 *>(adst + A_TERM_BYTES + kg * 128) =
+                        make_uint4(w1[4 * kg], w1[4 * kg + 1], w1[4 * kg + 2], w1[4 * kg + 3]);
+                    if (A_TERMS == 3)
+                        *reinterpret_cast<uint4 *>(adst + 2 * A_TERM_BYTES + kg * 128) =
+                            make_uint4(w2[4 * kg], w2[4 * kg + 1], w2[4 * kg + 2], w2[4 * kg + 3]);
+                }
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(smem_u32(&s_empty[s]));
-                    mbar_arrive(smem_u32(&o_full[o]));
+                    mbar_arrive(smem_u32(&s_empty[rs.idx]));
+                    mbar_arrive(smem_u32(&o_full[ro.idx]));
                 }
             }
             if (!ok) break;
@@ -273,7 +327,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
             sref_prev = sref;
         }
         if (ok && prev_tile >= 0) epilogue(prev_tile, lt - 1, sref_prev);
-        if (bad) atomicOr(prm.err, DEV_ERR_NONFINITE);
+        // exponent fields above float32's range (including inf / nan, 0x7FF) are reported
+        if (efmax > (1150u << 20)) atomicOr(prm.err, DEV_ERR_NONFINITE);
     }
 
     tc_fence_before();
@@ -289,6 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
 // ----------------------------------------------------------------------------
 namespace synth {
 constexpr int STG_BYTES = 32 * 16 * 8;  // TMA store box [32 rows][16 float64], 128B swizzle
+constexpr int JB = 32;                  // polar cells per tile in polar-block mode
 }
 
 struct SynthParams {
@@ -297,9 +353,21 @@ struct SynthParams {
     const float *Itc;      // [T][n_t]  Ith / dmu
     int *err;
     long long R;
-    int n_t, L, KL, P, Kpad, NC, n_nc, n_tiles, ns_b;
+    int n_r, n_t, L, KL, T, P, Kpad, NC, n_nc, ns_b;
+    int jblock;            // 1: tiles of (128/JB shells x JB polar cells), table slice in shared memory
+    int n_ib;              // shell blocks per polar block (polar-block mode)
+    int n_items;           // tiles in total
     uint32_t bchunk;       // bytes of one B chunk (3 terms)
 };
+
+// Tile -> (first shell, first polar cell) in polar-block mode; rows r of the
+// tile are (shell i0 + r / JB, polar cell j0 + r % JB).
+__device__ __forceinline__ void synth_item(const SynthParams &prm, int item, int &i0, int &j0)
+{
+    const int jb = item / prm.n_ib, ib = item % prm.n_ib;
+    i0 = ib * (kBM / synth::JB);
+    j0 = jb * synth::JB;
+}
 
 template <int A_TERMS, int NPROD>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -311,20 +379,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int NS_B = prm.ns_b;
     const int Kpad = prm.Kpad, NC = prm.NC;
     const int a_term_bytes = kBM * Kpad * 2;
+    const int SB = kBM / JB;
     uint8_t *stg = smem;                                          // [8 warps][2][4096]
     uint8_t *sA = stg + (size_t)kConvWarps * 2 * STG_BYTES;       // [A_TERMS][128 x Kpad]
     uint8_t *sB = sA + (size_t)A_TERMS * a_term_bytes;            // [NS_B][bchunk]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)NS_B * prm.bchunk);
+    float *sItc = reinterpret_cast<float *>(sB + (size_t)NS_B * prm.bchunk);  // [T][JB] (polar-block mode)
+    float *sC = sItc + (prm.jblock ? (size_t)prm.T * JB : 0);     // [SB][KL] (polar-block mode)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(
+        (reinterpret_cast<uintptr_t>(sC + (prm.jblock ? (size_t)SB * prm.KL : 0)) + 15) & ~uintptr_t(15));
     uint64_t *a_full = bars, *a_empty = bars + 1;
     uint64_t *b_full = bars + 2, *b_empty = b_full + NS_B;
     uint64_t *acc_full = b_empty + NS_B, *acc_empty = acc_full + 2, *drain = acc_empty + 2;
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *c_free = drain + 1, *c_ready = drain + 2;  // compute warps: staged rows free / loaded
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 3);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t ncols = tmem_ncols_for(2 * NC);
     const uint32_t acc_stride = ncols / 2;
     const int nkk = Kpad / 16;
+    // contiguous range of tiles of this CTA (consecutive tiles share a polar block)
+    const int it0 = (int)((long long)prm.n_items * blockIdx.x / gridDim.x);
+    const int it1 = (int)((long long)prm.n_items * (blockIdx.x + 1) / gridDim.x);
 
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(a_full), kConvWarps);
@@ -338,6 +414,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(smem_u32(&acc_empty[b]), kConvWarps);
         }
         mbar_init(smem_u32(drain), 1);
+        mbar_init(smem_u32(c_free), kConvWarps);
+        mbar_init(smem_u32(c_ready), kConvWarps);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -353,26 +431,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         // ---------------- producer: table chunks (nc, kk) for every tile
         if (lane == 0) {
-            uint32_t g = 0;
-            long long last_g = -1;
+            Ring rb;
+            int issued = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x)
+            for (int it = it0; it < it1 && ok; ++it)
                 for (int nc = 0; nc < prm.n_nc && ok; ++nc)
-                    for (int kk = 0; kk < nkk; ++kk, ++g) {
-                        const int s = g % NS_B;
-                        ok = mbar_wait(smem_u32(&b_empty[s]), ((g / NS_B) & 1) ^ 1, abort_flag, prm.err);
+                    for (int kk = 0; kk < nkk; ++kk, rb.next(NS_B)) {
+                        ok = mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err);
                         if (!ok) break;
-                        mbar_arrive_expect_tx(smem_u32(&b_full[s]), prm.bchunk);
-                        bulk_load(smem_u32(sB + (size_t)s * prm.bchunk),
-                                  prm.tabT + ((size_t)nc * nkk + kk) * prm.bchunk, prm.bchunk, smem_u32(&b_full[s]));
-                        last_g = g;
+                        mbar_arrive_expect_tx(smem_u32(&b_full[rb.idx]), prm.bchunk);
+                        bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bchunk),
+                                  prm.tabT + ((size_t)nc * nkk + kk) * prm.bchunk, prm.bchunk,
+                                  smem_u32(&b_full[rb.idx]));
+                        ++issued;
                     }
-            if (*abort_flag && last_g >= 0) {
-                for (long long gg = last_g; gg >= 0 && gg > last_g - NS_B; --gg) {
-                    const int s = (int)(gg % NS_B);
-                    const uint32_t ph = (uint32_t)((gg / NS_B) & 1);
+            if (*abort_flag && issued > 0) {
+                Ring back = rb;
+                for (int n = 0; n < NS_B && n < issued; ++n) {
+                    back.idx = (back.idx == 0) ? NS_B - 1 : back.idx - 1;
+                    if (back.idx == NS_B - 1) back.phase ^= 1u;
                     const long long t0 = clock64();
-                    while (!mbar_try_wait(smem_u32(&b_full[s]), ph) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
+                    while (!mbar_try_wait(smem_u32(&b_full[back.idx]), back.phase) &&
+                           clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
                     }
                 }
             }
@@ -382,10 +462,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(kBM, NC);
             const uint32_t sbo_a = (uint32_t)Kpad * 16;
-            uint32_t g = 0, u = 0;
+            Ring rb;
+            uint32_t u = 0;
             int lt = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ++lt) {
+            for (int it = it0; it < it1 && ok; ++it, ++lt) {
                 ok = mbar_wait(smem_u32(a_full), lt & 1, abort_flag, prm.err);
                 if (!ok) break;
                 tc_fence_after();
@@ -395,13 +476,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)buf * acc_stride;
-                    for (int kk = 0; kk < nkk; ++kk, ++g) {
-                        const int s = g % NS_B;
-                        ok = mbar_wait(smem_u32(&b_full[s]), (g / NS_B) & 1, abort_flag, prm.err);
+                    for (int kk = 0; kk < nkk; ++kk, rb.next(NS_B)) {
+                        ok = mbar_wait(smem_u32(&b_full[rb.idx]), rb.phase, abort_flag, prm.err);
                         if (!ok) break;
                         tc_fence_after();
                         const uint32_t a_base = smem_u32(sA) + (uint32_t)(kk * 256);
-                        const uint32_t b_base = smem_u32(sB + (size_t)s * prm.bchunk);
+                        const uint32_t b_base = smem_u32(sB + (size_t)rb.idx * prm.bchunk);
 #pragma unroll
                         for (int pi = 0; pi < NPROD; ++pi) {
                             const uint64_t ad =
@@ -409,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint64_t bd = sdesc_noswizzle(b_base + (uint32_t)(c_prod_b[pi] * NC * 32), 128, 256);
                             umma_bf16(d_tmem, ad, bd, idesc, (kk | pi) != 0);
                         }
-                        umma_commit(smem_u32(&b_empty[s]));
+                        umma_commit(smem_u32(&b_empty[rb.idx]));
                     }
                     if (!ok) break;
                     umma_commit(smem_u32(&acc_full[buf]));
@@ -426,35 +506,100 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- theta synthesis (A operand) + epilogue (Phi)
         const int cw = warp - 2, qd = warp & 3, half = cw >> 2;
         const int row = qd * 32 + lane;
+        const int ctid = threadIdx.x - 64;  // 0..255 among the compute warps
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
-        const int n_t = prm.n_t, L = prm.L, KL = prm.KL, P = prm.P;
+        const int n_t = prm.n_t, L = prm.L, KL = prm.KL;
         uint32_t u = 0, cs = 0;
-        int lt = 0;
+        int lt = 0, cur_j0 = -1;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ++lt) {
+        for (int it = it0; it < it1 && ok; ++it, ++lt) {
             ok = warp_all(mbar_wait(smem_u32(a_empty), (lt & 1) ^ 1, abort_flag, prm.err));
             if (!ok) break;
-            const long long grow = (long long)tile * kBM + row;
-            const bool valid = grow < prm.R;
-            const int i = valid ? (int)(grow / n_t) : 0;
-            const int j = valid ? (int)(grow % n_t) : 0;
-            const float *crow = prm.C32 + (size_t)i * KL;
-            float g0 = 0.0f;
-            if (valid)
-                for (int l = 0; l <= L; ++l) g0 = fmaf(prm.Itc[(size_t)tri(l, 0) * n_t + j], crow[l * l], g0);
-            // A operand: G[row][p], p = 1..2L, stored at K index p-1, in A_TERMS bf16 terms
+            // rows of this tile: (shell i, polar cell j) and the first memory row of this warp's box
+            int i, j;
+            long long box_row;
+            bool valid;
+            const float *crow;    // coefficients C[i][*] of this row's shell
+            const float *itab;    // table Itc[t][j], stride tstride in t
+            int tstride;
+            if (prm.jblock) {
+                int i0, j0;
+                synth_item(prm, it, i0, j0);
+                i = i0 + row / JB;
+                j = j0 + row % JB;
+                valid = i < prm.n_r;
+                box_row = (long long)(i0 + (qd * 32) / JB) * n_t + j0 + (qd * 32) % JB;
+                // every compute warp is done with the previous tile's staged rows
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(c_free));
+                ok = warp_all(mbar_wait(smem_u32(c_free), lt & 1, abort_flag, prm.err));
+                if (!ok) break;
+                if (j0 != cur_j0) {
+                    for (int e = ctid; e < prm.T * JB; e += 256)
+                        sItc[e] = __ldg(prm.Itc + (size_t)(e / JB) * n_t + j0 + e % JB);
+                    cur_j0 = j0;
+                }
+                for (int e = ctid; e < SB * KL; e += 256) {
+                    const int si = i0 + e / KL;
+                    sC[e] = (si < prm.n_r) ? __ldg(prm.C32 + (size_t)si * KL + e % KL) : 0.0f;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(c_ready));
+                ok = warp_all(mbar_wait(smem_u32(c_ready), lt & 1, abort_flag, prm.err));
+                if (!ok) break;
+                crow = sC + (row / JB) * KL;
+                itab = sItc + row % JB;
+                tstride = JB;
+            } else {
+                const long long grow = (long long)it * kBM + row;
+                valid = grow < prm.R;
+                i = valid ? (int)(grow / n_t) : 0;
+                j = valid ? (int)(grow % n_t) : 0;
+                box_row = (long long)it * kBM + qd * 32;
+                crow = prm.C32 + (size_t)i * KL;
+                itab = prm.Itc + j;
+                tstride = n_t;
+            }
+            (void)i;
+            (void)j;
+            float g0 = 0.0f, g1 = 0.0f;
+            if (valid) {
+                int l = 0;
+                for (; l + 1 <= L; l += 2) {
+                    g0 = fmaf(itab[(size_t)tri(l, 0) * tstride], crow[l * l], g0);
+                    g1 = fmaf(itab[(size_t)tri(l + 1, 0) * tstride], crow[(l + 1) * (l + 1)], g1);
+                }
+                if (l <= L) g0 = fmaf(itab[(size_t)tri(l, 0) * tstride], crow[l * l], g0);
+                g0 += g1;
+            }
+            // A operand: G[row][p], p = 1..2L, stored at K index p-1, in A_TERMS bf16 terms.
+            // Group gi holds p = 8 gi + 1 .. 8 gi + 8, the cos/sin pairs of m = 4 gi + 1 .. 4 gi + 4;
+            // each table value serves both members of a pair.
             for (int gi = half; gi < Kpad / 8; gi += 2) {
                 float gv[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int p = gi * 8 + e + 1;
-                    float acc = 0.0f;
-                    if (valid && p < P) {
-                        const int m = pcol_m(p);
-                        for (int l = m; l <= L; ++l)
-                            acc = fmaf(prm.Itc[(size_t)tri(l, m) * n_t + j], crow[l * l + p], acc);
+                for (int mm = 0; mm < 4; ++mm) {
+                    const int m = 4 * gi + mm + 1;
+                    float ac = 0.0f, as = 0.0f, bc = 0.0f, bs = 0.0f;
+                    if (valid && m <= L) {
+                        const float *cc = crow + 2 * m - 1;  // C[i][l^2 + 2m - 1], C[i][l^2 + 2m]
+                        int l = m;
+                        for (; l + 1 <= L; l += 2) {
+                            const float w0 = itab[(size_t)tri(l, m) * tstride];
+                            const float w1 = itab[(size_t)tri(l + 1, m) * tstride];
+                            ac = fmaf(w0, cc[l * l], ac);
+                            as = fmaf(w0, cc[l * l + 1], as);
+                            bc = fmaf(w1, cc[(l + 1) * (l + 1)], bc);
+                            bs = fmaf(w1, cc[(l + 1) * (l + 1) + 1], bs);
+                        }
+                        if (l <= L) {
+                            const float w0 = itab[(size_t)tri(l, m) * tstride];
+                            ac = fmaf(w0, cc[l * l], ac);
+                            as = fmaf(w0, cc[l * l + 1], as);
+                        }
                     }
-                    gv[e] = acc;
+                    gv[2 * mm] = ac + bc;
+                    gv[2 * mm + 1] = as + bs;
                 }
                 uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
@@ -477,32 +622,53 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(a_full));
 
+            // a box of 32 rows is written only when its first row is a real row
+            const bool box_valid = prm.jblock ? (__shfl_sync(kFull, valid ? 1 : 0, 0) != 0) : (box_row < prm.R);
+            int nc_cur = 0;
+            // converts 16 accumulator columns of this row (+ the m = 0 term) to float64 in a
+            // swizzled staging box and hands the box to a TMA store
+            auto store_chunk = [&](const uint32_t(&v)[16], int ch) {
+                uint8_t *st = stg + (size_t)(cw * 2 + (cs & 1)) * STG_BYTES;
+                ++cs;
+                if (lane == 0) bulk_wait_read_le1();
+                __syncwarp();
+                uint8_t *srow = st + lane * 128;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    uint32_t lo0, hi0, lo1, hi1;
+                    f32_to_f64w_finite(__uint_as_float(v[2 * e]) + g0, lo0, hi0);
+                    f32_to_f64w_finite(__uint_as_float(v[2 * e + 1]) + g0, lo1, hi1);
+                    *reinterpret_cast<uint4 *>(srow + ((e ^ (lane & 7)) << 4)) = make_uint4(lo0, hi0, lo1, hi1);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0 && box_valid) {
+                    tma_store_2d(&tmPhi, smem_u32(st), nc_cur * NC + ch * 16, (int)box_row);
+                    bulk_commit();
+                }
+            };
             for (int nc = 0; nc < prm.n_nc && ok; ++nc, ++u) {
+                nc_cur = nc;
                 const int buf = u & 1;
                 ok = warp_all(mbar_wait(smem_u32(&acc_full[buf]), (u >> 1) & 1, abort_flag, prm.err));
                 if (!ok) break;
                 tc_fence_after();
-                for (int ch = half; ch < NC / 16; ch += 2, ++cs) {
-                    uint32_t v[16];
-                    tmem_ld16(tmem_base + lane_base + (uint32_t)buf * acc_stride + (uint32_t)(ch * 16), v);
-                    tmem_ld_wait();
-                    uint8_t *st = stg + (size_t)(cw * 2 + (cs & 1)) * STG_BYTES;
-                    if (lane == 0) bulk_wait_read_le1();
-                    __syncwarp();
-                    uint8_t *srow = st + lane * 128;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        uint32_t lo0, hi0, lo1, hi1;
-                        f32_to_f64w(__uint_as_float(v[2 * e]) + g0, lo0, hi0);
-                        f32_to_f64w(__uint_as_float(v[2 * e + 1]) + g0, lo1, hi1);
-                        *reinterpret_cast<uint4 *>(srow + ((e ^ (lane & 7)) << 4)) = make_uint4(lo0, hi0, lo1, hi1);
-                    }
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    // boxes that start past the last row are skipped (nothing to write)
-                    if (lane == 0 && (long long)tile * kBM + qd * 32 < prm.R) {
-                        tma_store_2d(&tmPhi, smem_u32(st), nc * NC + ch * 16, tile * kBM + qd * 32);
-                        bulk_commit();
+                // 16-column chunks ch = half, half + 2, ...; the tensor-memory load of the
+                // next chunk is in flight while the current one is converted and stored
+                const int nch = NC / 16;
+                const uint32_t tcol = tmem_base + lane_base + (uint32_t)buf * acc_stride;
+                uint32_t va[16], vb[16];
+                if (half < nch) tmem_ld16(tcol + (uint32_t)(half * 16), va);
+                tmem_ld_wait();
+                for (int ch = half; ch < nch; ch += 4) {
+                    const bool nb = ch + 2 < nch, na = ch + 4 < nch;
+                    if (nb) tmem_ld16(tcol + (uint32_t)((ch + 2) * 16), vb);
+                    store_chunk(va, ch);
+                    if (nb) {
+                        tmem_ld_wait();
+                        if (na) tmem_ld16(tcol + (uint32_t)((ch + 4) * 16), va);
+                        store_chunk(vb, ch + 2);
+                        if (na) tmem_ld_wait();
                     }
                 }
                 tc_fence_before();
@@ -543,12 +709,13 @@ __device__ __forceinline__ size_t canon_off(int n, int kk)
     return (size_t)(n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2;
 }
 
-// projection B: chunk kc, term tb, row p (N), column kk (K = azimuthal cell)
+// projection B: chunk kc, term tb, row p (N), column kk (K = azimuthal cell), 32 cells per chunk
 __global__ void k_tab_proj(const double *__restrict__ Iph, int n_p, int P, int Npad, int n_kc, uint8_t *__restrict__ tab,
                            float *__restrict__ colsum)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)n_kc * Npad * 16;
+    constexpr int BK = proj::BK;
+    const long long total = (long long)n_kc * Npad * BK;
     if (idx < Npad && colsum) {
         double s = 0.0;
         if (idx < P)
@@ -556,18 +723,19 @@ __global__ void k_tab_proj(const double *__restrict__ Iph, int n_p, int P, int N
         colsum[idx] = (float)s;
     }
     if (idx >= total) return;
-    const int kc = (int)(idx / (Npad * 16));
-    const int rem = (int)(idx % (Npad * 16));
-    const int p = rem / 16, kk = rem % 16;
-    const int k = kc * 16 + kk;
+    const int kc = (int)(idx / (Npad * BK));
+    const int rem = (int)(idx % (Npad * BK));
+    const int p = rem / BK, kk = rem % BK;
+    const int k = kc * BK + kk;
     const double v = (p < P && k < n_p) ? Iph[(size_t)p * n_p + k] : 0.0;
     uint16_t b0, b1, b2;
     split3(v, b0, b1, b2);
-    uint8_t *base = tab + (size_t)kc * 3 * Npad * 32;
-    const size_t off = canon_off(p, kk);
+    const size_t term = (size_t)Npad * BK * 2;
+    uint8_t *base = tab + (size_t)kc * 3 * term;
+    const size_t off = (size_t)(p >> 3) * proj::SBO + (kk >> 3) * 128 + (p & 7) * 16 + (kk & 7) * 2;
     *reinterpret_cast<uint16_t *>(base + off) = b0;
-    *reinterpret_cast<uint16_t *>(base + (size_t)Npad * 32 + off) = b1;
-    *reinterpret_cast<uint16_t *>(base + (size_t)2 * Npad * 32 + off) = b2;
+    *reinterpret_cast<uint16_t *>(base + term + off) = b1;
+    *reinterpret_cast<uint16_t *>(base + 2 * term + off) = b2;
 }
 
 // synthesis B: chunk (nc, kc), term tb, row n (N = azimuthal cell), column kk (K = p - 1)
@@ -617,14 +785,15 @@ cudaError_t set_smem_attrs(int proj_smem, int synth_smem)
 
 int proj_smem_bytes(const SplitPlan &pl, int ns_s, int ns_o)
 {
-    const int bchunk = 3 * pl.Npad * 32;
-    return 1024 + ns_s * proj::S_BYTES + ns_s * bchunk + ns_o * pl.a_terms * proj::A_TERM_BYTES + 256;
+    const int bchunk = 3 * pl.Npad * proj::BK * 2;
+    return 1024 + ns_s * proj::S_BYTES + ns_s * bchunk + ns_o * pl.a_terms * proj::A_TERM_BYTES + 512;
 }
 
-int synth_smem_bytes(const SplitPlan &pl, int ns_b)
+int synth_smem_bytes(const SplitPlan &pl, int ns_b, int jblock, int T, int KL)
 {
     const int bchunk = 3 * pl.NC * 32;
-    return 1024 + kConvWarps * 2 * synth::STG_BYTES + pl.a_terms * kBM * pl.Kpad * 2 + ns_b * bchunk + 256;
+    const int tabs = jblock ? (T * synth::JB + (kBM / synth::JB) * KL) * 4 + 16 : 0;
+    return 1024 + kConvWarps * 2 * synth::STG_BYTES + pl.a_terms * kBM * pl.Kpad * 2 + ns_b * bchunk + tabs + 256;
 }
 
 constexpr int kSmemLimit = 232448;  // 227 KB opt-in per block on sm_100-class parts
@@ -635,14 +804,22 @@ constexpr int kSmemLimit = 232448;  // 227 KB opt-in per block on sm_100-class p
 int split_smem_limits(mp_mesh *m)
 {
     SplitPlan &pl = m->plan;
-    int ns_s = 6;
-    while (ns_s > 2 && proj_smem_bytes(pl, ns_s, 4) > kSmemLimit) --ns_s;
-    if (proj_smem_bytes(pl, ns_s, 4) > kSmemLimit) return 1;
+    int ns_s = 4;
+    while (ns_s > 2 && proj_smem_bytes(pl, ns_s, 2) > kSmemLimit) --ns_s;
+    if (proj_smem_bytes(pl, ns_s, 2) > kSmemLimit) return 1;
+    // polar-block tiles when the polar cells split into blocks of 32 and the table slice fits
+    int jblock = (m->n_t % synth::JB == 0) ? 1 : 0;
     int ns_b = 3;
-    while (ns_b > 2 && synth_smem_bytes(pl, ns_b) > kSmemLimit) --ns_b;
-    if (synth_smem_bytes(pl, ns_b) > kSmemLimit) return 2;
-    pl.proj_smem = proj_smem_bytes(pl, ns_s, 4);
-    pl.synth_smem = synth_smem_bytes(pl, ns_b);
+    while (ns_b > 2 && synth_smem_bytes(pl, ns_b, jblock, m->T, m->KL) > kSmemLimit) --ns_b;
+    if (jblock && synth_smem_bytes(pl, ns_b, jblock, m->T, m->KL) > kSmemLimit) {
+        jblock = 0;
+        ns_b = 3;
+        while (ns_b > 2 && synth_smem_bytes(pl, ns_b, 0, m->T, m->KL) > kSmemLimit) --ns_b;
+    }
+    if (synth_smem_bytes(pl, ns_b, jblock, m->T, m->KL) > kSmemLimit) return 2;
+    pl.jblock = jblock;
+    pl.proj_smem = proj_smem_bytes(pl, ns_s, 2);
+    pl.synth_smem = synth_smem_bytes(pl, ns_b, jblock, m->T, m->KL);
     pl.ns_s = ns_s;
     pl.ns_b = ns_b;
     return 0;
@@ -652,7 +829,7 @@ cudaError_t launch_split_tables(mp_mesh *m)
 {
     SplitPlan &pl = m->plan;
     {
-        const long long n = std::max<long long>((long long)pl.n_kc * pl.Npad * 16, pl.Npad);
+        const long long n = std::max<long long>((long long)pl.n_kc * pl.Npad * proj::BK, pl.Npad);
         k_tab_proj<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(m->d_Iph, m->n_p, m->P, pl.Npad, pl.n_kc,
                                                                        m->d_tabB, m->d_colsum);
     }
@@ -683,12 +860,13 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho)
     prm.F = m->d_F32;
     prm.err = m->d_err;
     prm.R = m->R;
+    prm.n_p = m->n_p;
     prm.n_kc = pl.n_kc;
     prm.Npad = pl.Npad;
     prm.n_tiles = (int)((m->R + kBM - 1) / kBM);
     prm.ns_s = pl.ns_s;
-    prm.ns_o = 4;
-    prm.bchunk = (uint32_t)(3 * pl.Npad * 32);
+    prm.ns_o = 2;
+    prm.bchunk = (uint32_t)(3 * pl.Npad * proj::BK * 2);
     const int grid = std::min(prm.n_tiles, pl.proj_ctas);
     cudaEvent_t ev;
     prof_begin(m, "split_phi_project_tc", &ev);
@@ -710,17 +888,27 @@ cudaError_t launch_split_synth(mp_mesh *m, double *phi)
     prm.Itc = m->d_Itc32;
     prm.err = m->d_err;
     prm.R = m->R;
+    prm.n_r = m->n_r;
     prm.n_t = m->n_t;
     prm.L = m->L;
     prm.KL = m->KL;
+    prm.T = m->T;
     prm.P = m->P;
     prm.Kpad = pl.Kpad;
     prm.NC = pl.NC;
     prm.n_nc = pl.n_nc;
-    prm.n_tiles = (int)((m->R + kBM - 1) / kBM);
     prm.ns_b = pl.ns_b;
+    prm.jblock = pl.jblock;
+    if (pl.jblock) {
+        const int SB = kBM / synth::JB;
+        prm.n_ib = (m->n_r + SB - 1) / SB;
+        prm.n_items = prm.n_ib * (m->n_t / synth::JB);
+    } else {
+        prm.n_ib = 0;
+        prm.n_items = (int)((m->R + kBM - 1) / kBM);
+    }
     prm.bchunk = (uint32_t)(3 * pl.NC * 32);
-    const int grid = std::min(prm.n_tiles, pl.synth_ctas);
+    const int grid = std::min(prm.n_items, pl.synth_ctas);
     cudaEvent_t ev;
     prof_begin(m, "split_synth_tc", &ev);
     if (pl.a_terms == 2)

@@ -223,6 +223,23 @@ __device__ __forceinline__ float f64w_to_f32(uint32_t lo, uint32_t hi)
 
 __device__ __forceinline__ bool f64w_nonfinite(uint32_t hi) { return (hi & 0x7FF00000u) == 0x7FF00000u; }
 
+// Same conversion, cheaper: the low nine exponent bits and the top 23 mantissa
+// bits come out of one 64-bit shift (after adding half a float32 ulp for
+// round-half-up); for exponents inside the float32 normal range the float32
+// exponent field is then the low eight float64 exponent bits with the top bit
+// flipped.  Magnitudes outside [2^-126, 2^128) give a signed zero; the caller
+// tracks ef = hi & 0x7FF00000 (returned) to flag values too large for float32.
+__device__ __forceinline__ float f64w_to_f32_fast(uint32_t lo, uint32_t hi, uint32_t &ef)
+{
+    const unsigned long long v = ((static_cast<unsigned long long>(hi) << 32) | lo) + (1ull << 28);
+    const uint32_t t = static_cast<uint32_t>(v >> 29);
+    const uint32_t sign = hi & 0x80000000u;
+    uint32_t r = ((t & 0x7FFFFFFFu) | sign) ^ 0x40000000u;
+    ef = hi & 0x7FF00000u;
+    r = (ef - (897u << 20) < (254u << 20)) ? r : sign;
+    return __uint_as_float(r);
+}
+
 // float32 -> float64 words, exact for normal numbers, integer ops only.
 __device__ __forceinline__ void f32_to_f64w(float x, uint32_t &lo, uint32_t &hi)
 {
@@ -236,6 +253,19 @@ __device__ __forceinline__ void f32_to_f64w(float x, uint32_t &lo, uint32_t &hi)
     h = (mag >= 0x7F800000u) ? (sign | 0x7FF00000u | ((mag & 0x7FFFFFu) ? 0x80000u : 0u)) : h;
     lo = l;
     hi = h;
+}
+
+// float32 -> float64 words for finite x: exact for normal numbers, zero (with
+// sign) for zeros and float32 subnormals.  Non-finite inputs are not preserved.
+__device__ __forceinline__ void f32_to_f64w_finite(float x, uint32_t &lo, uint32_t &hi)
+{
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t sign = b & 0x80000000u;
+    const uint32_t mag = b & 0x7FFFFFFFu;
+    const uint32_t h = ((mag >> 3) + 0x38000000u) | sign;
+    const bool normal = mag >= 0x00800000u;
+    hi = normal ? h : sign;
+    lo = normal ? (b << 29) : 0u;
 }
 
 // Round-to-nearest bf16 pair packed in one word (x in the low half).

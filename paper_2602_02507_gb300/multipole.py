@@ -68,6 +68,7 @@ def load_library(path: str = LIB_PATH):
         "mp_batch_destroy": [vp],
         "mp_autotune": [vp, ctypes.c_char_p],
         "mp_last_error_detail": [ctypes.c_char_p, i],
+        "mp_probe_rates": [dp, dp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -254,6 +255,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def probe_rates() -> dict:
+    """Measured float64 FMA rate (TFLOP/s) and float64->float32 conversion rate of the current device."""
+    lib = load_library()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib.mp_probe_rates(ctypes.byref(a), ctypes.byref(b)), "mp_probe_rates")
+    return {"fp64_tflops": a.value, "cvt_f64_f32_per_s": b.value}
 
 
 def status_string(code: int) -> str:

@@ -12,7 +12,7 @@ reasons of conditioning, not of arithmetic).
 import numpy as np
 import pytest
 
-from gpu_helpers import gpu_solve, oracle_solve, per_l_errors, phi_rel_err, significant_degrees
+from gpu_helpers import edge_moment_errors, gpu_solve, oracle_solve, per_l_errors, phi_rel_err
 from paper_2602_02507_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -57,11 +57,9 @@ def test_fp64_path_matches_oracle(name):
     assert phi_rel_err(got["phi"], ref["phi"]) <= 1e-12
     L = w.mesh.L
     assert max(per_l_errors(got["A"], ref["A"], L)) <= 1e-12
-    # edge moments scale differently per degree: compare each significant degree on its own
-    for key in ("MR", "MI"):
-        errs = per_l_errors(got[key], ref[key], L, floor=0.0)
-        for l in significant_degrees(ref["A"], L):
-            assert errs[l] <= 1e-12, (key, l, errs[l])
+    # edge moments: per degree, against the size of the terms each recurrence adds
+    for key, errs in edge_moment_errors(got, ref).items():
+        assert max(errs) <= 1e-12, (key, errs)
 
 
 SPLIT_CASES = {
