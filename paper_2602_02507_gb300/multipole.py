@@ -69,6 +69,7 @@ def load_library(path: str = LIB_PATH):
         "mp_autotune": [vp, ctypes.c_char_p],
         "mp_last_error_detail": [ctypes.c_char_p, i],
         "mp_probe_rates": [dp, dp],
+        "mp_moments_noalloc": [vp, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -196,6 +197,14 @@ class Mesh:
         p = [None if t is None else ctypes.c_void_p(_tensor_ptr(t, s, nm))
              for t, s, nm in ((ang, n_r * K, "ang"), (mr, (n_r + 1) * K, "mr"), (mi, (n_r + 1) * K, "mi"))]
         _check(self._lib.mp_get_moments(self._h, *p), "mp_get_moments")
+
+    def moments_noalloc(self, rho, out):
+        """Angular moments of rho into out [n_r * K_L] without device allocation
+        (mp_moments_noalloc; for callers that cannot allocate at the point of use)."""
+        _check(self._lib.mp_moments_noalloc(self._h, ctypes.c_void_p(_tensor_ptr(rho, self.cells, "rho")),
+                                            ctypes.c_void_p(_tensor_ptr(out, self.shape[0] * self.n_moments,
+                                                                        "out"))),
+               "mp_moments_noalloc")
 
     def synchronize(self):
         _check(self._lib.mp_mesh_synchronize(self._h), "mp_mesh_synchronize")
