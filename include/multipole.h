@@ -142,7 +142,11 @@ MP_API mp_status mp_set_phi_output(mp_mesh *mesh, double *phi_dev);
 
 /*
  * Run steps (a)-(d) on the mesh's stream: reads the bound density, writes Phi
- * and keeps the moments of this solve for mp_get_moments().
+ * and keeps the moments of this solve for mp_get_moments().  The kernel chain
+ * is captured once as a CUDA graph (on a private stream, at the first solve
+ * and again after the bound buffers change or mp_autotune) and replayed by one
+ * graph launch per solve; with profiling enabled the kernels are launched one
+ * by one instead, with events between them.
  * Errors: MP_ERR_NOT_READY (no density bound), MP_ERR_OOM, MP_ERR_CUDA;
  * device-side errors surface at mp_mesh_synchronize().
  */
@@ -197,8 +201,10 @@ MP_API mp_status mp_batch_solve(mp_batch *batch);
 MP_API mp_status mp_batch_destroy(mp_batch *batch);
 
 /*
- * Pick tile and launch parameters for the mesh by timing candidates on the
- * device (needs a bound density and output); the choice is cached in
+ * Pick launch parameters for the mesh by timing candidates on the device
+ * (needs a bound density): the projection's density ring depth, the
+ * synthesis table ring depth (when the table is not resident) and the threads
+ * per moment column of the radial recurrences.  The choice is cached in
  * cache_path (a text file, may be NULL) keyed by (n_r, n_theta, n_phi, l_max,
  * precision) and reused by later meshes of the same key.
  */

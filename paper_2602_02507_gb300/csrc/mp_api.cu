@@ -153,9 +153,9 @@ static mp_status dalloc(mp_mesh *m, T **p, size_t count)
 static void free_mesh_buffers(mp_mesh *m)
 {
     void *ptrs[] = {m->d_r,   m->d_Ith,  m->d_dmu,    m->d_Iph,   m->d_Iphc,   m->d_WR,    m->d_WI,
-                    m->d_RR,  m->d_RI,   m->d_V,      m->d_A,     m->d_MR,     m->d_MI,    m->d_C,
-                    m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_IthT32, m->d_Itc32, m->d_colsum,
-                    m->d_tabB, m->d_tabT, m->phi_own, m->rho_stage, m->d_err};
+                    m->d_GR,  m->d_GI,   m->d_V,      m->d_A,     m->d_MR,     m->d_MI,    m->d_C,
+                    m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_Ith32, m->d_Itc32, m->d_colsum,
+                    m->d_tabB, m->d_tabT, m->d_Aop, m->d_G0, m->phi_own, m->rho_stage, m->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &pe : m->prof_pending) {
@@ -179,6 +179,15 @@ struct DeviceGuard {
         if (prev >= 0 && cur != prev) cudaSetDevice(prev);
     }
 };
+
+static void drop_graph(mp_mesh *m)
+{
+    if (m->g_exec) cudaGraphExecDestroy(m->g_exec);
+    if (m->g_graph) cudaGraphDestroy(m->g_graph);
+    m->g_exec = nullptr;
+    m->g_graph = nullptr;
+    m->g_rho = m->g_phi = nullptr;
+}
 
 static mp_status ensure_phi_own(mp_mesh *m)
 {
@@ -213,6 +222,44 @@ static mp_status run_solve(mp_mesh *m, const double *rho, double *phi)
     return MP_OK;
 }
 
+// The solve's kernel chain replayed as one CUDA graph launch on the mesh stream.
+// The graph is captured on a private stream (the caller's stream may be the
+// legacy default stream, which cannot be captured) and captured again when the
+// bound density or potential buffer changes.
+static mp_status solve_graph(mp_mesh *m, const double *rho, double *phi)
+{
+    if (!m->g_exec || m->g_rho != rho || m->g_phi != phi) {
+        drop_graph(m);
+        if (!m->g_cap) MP_TRY(cudaStreamCreateWithFlags(&m->g_cap, cudaStreamNonBlocking));
+        cudaStream_t saved = m->stream;
+        m->stream = m->g_cap;
+        cudaError_t e = cudaStreamBeginCapture(m->g_cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            m->stream = saved;
+            return cuda_status(e, "cudaStreamBeginCapture");
+        }
+        mp_status st = run_solve(m, rho, phi);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(m->g_cap, &g);
+        m->stream = saved;
+        if (st != MP_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&m->g_exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_status(e, "cudaGraphInstantiate");
+        }
+        m->g_graph = g;
+        m->g_rho = rho;
+        m->g_phi = phi;
+    }
+    MP_TRY(cudaGraphLaunch(m->g_exec, m->stream));
+    return MP_OK;
+}
+
 static mp_status plan_split(mp_mesh *m)
 {
     SplitPlan &pl = m->plan;
@@ -221,6 +268,12 @@ static mp_status plan_split(mp_mesh *m)
     pl.Npad = round_up(m->P, 16);
     pl.n_kc = (m->n_p + 31) / 32;
     pl.Kpad = std::max(16, round_up(2 * m->L, 16));
+    {
+        // polar rows of F and the theta tables: whole float4 units plus an odd pad unit count,
+        // so that consecutive rows start on different shared-memory banks
+        const int nq = (m->n_t + 3) / 4;
+        pl.ldF = 4 * ((nq % 2 == 0) ? nq + 1 : nq + 2);
+    }
     pl.NC = std::min(256, round_up(m->n_p, 16));
     pl.n_nc = (m->n_p + pl.NC - 1) / pl.NC;
     pl.proj_ctas = m->num_sms;
@@ -346,8 +399,8 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
     ALLOC(m->d_Iphc, (size_t)m->P * n_phi);
     ALLOC(m->d_WR, (size_t)(l_max + 1) * n_r);
     ALLOC(m->d_WI, (size_t)(l_max + 1) * n_r);
-    ALLOC(m->d_RR, (size_t)(l_max + 1) * n_r);
-    ALLOC(m->d_RI, (size_t)(l_max + 1) * n_r);
+    ALLOC(m->d_GR, (size_t)(l_max + 1) * n_r);
+    ALLOC(m->d_GI, (size_t)(l_max + 1) * n_r);
     ALLOC(m->d_V, n_r);
     ALLOC(m->d_A, (size_t)n_r * m->KL);
     ALLOC(m->d_MR, (size_t)(n_r + 1) * m->KL);
@@ -361,15 +414,27 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
         st = plan_split(m);
         if (st != MP_OK) return fail(st);
         const SplitPlan &pl = m->plan;
-        ALLOC(m->d_F32, (size_t)m->R * pl.Npad);
+        ALLOC(m->d_F32, (size_t)n_r * m->P * pl.ldF);
         ALLOC(m->d_C32, (size_t)n_r * m->KL);
-        ALLOC(m->d_IthT32, (size_t)m->T * n_theta);
-        ALLOC(m->d_Itc32, (size_t)m->T * n_theta);
+        ALLOC(m->d_Ith32, (size_t)m->T * pl.ldF);
+        ALLOC(m->d_Itc32, (size_t)m->T * pl.ldF);
         ALLOC(m->d_colsum, pl.Npad);
         m->tabB_chunk_bytes = (size_t)3 * pl.Npad * 64;
         m->tabT_chunk_bytes = (size_t)3 * pl.NC * 32;
         ALLOC(m->d_tabB, m->tabB_chunk_bytes * pl.n_kc);
         ALLOC(m->d_tabT, m->tabT_chunk_bytes * pl.n_nc * (pl.Kpad / 16));
+        {
+            const size_t tiles = (size_t)((m->R + 127) / 128);
+            ALLOC(m->d_Aop, tiles * pl.a_terms * 128 * pl.Kpad * 2);
+            ALLOC(m->d_G0, tiles * 128);
+            // rows past the last one in the final tile are never written by the theta synthesis
+            cudaMemsetAsync(m->d_Aop, 0, tiles * pl.a_terms * 128 * pl.Kpad * 2, m->stream);
+            cudaMemsetAsync(m->d_G0, 0, tiles * 128 * sizeof(float), m->stream);
+            // padding cells of the polar rows stay zero: the theta contraction sums over them
+            cudaMemsetAsync(m->d_F32, 0, (size_t)n_r * m->P * pl.ldF * sizeof(float), m->stream);
+            cudaMemsetAsync(m->d_Ith32, 0, (size_t)m->T * pl.ldF * sizeof(float), m->stream);
+            cudaMemsetAsync(m->d_Itc32, 0, (size_t)m->T * pl.ldF * sizeof(float), m->stream);
+        }
     }
 #undef ALLOC
     {
@@ -402,6 +467,8 @@ mp_status mp_mesh_destroy(mp_mesh *m)
     if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
     DeviceGuard dg(m->device);
     cudaStreamSynchronize(m->stream);
+    drop_graph(m);
+    if (m->g_cap) cudaStreamDestroy(m->g_cap);
     free_mesh_buffers(m);
     delete m;
     return MP_OK;
@@ -458,7 +525,9 @@ mp_status mp_solve(mp_mesh *m)
         if (st != MP_OK) return st;
         phi = m->phi_own;
     }
-    return run_solve(m, m->rho, phi);
+    // per-kernel timing needs events between the kernels: launch them one by one
+    if (m->profiling) return run_solve(m, m->rho, phi);
+    return solve_graph(m, m->rho, phi);
 }
 
 mp_status mp_get_phi(mp_mesh *m, double *phi_dev)
@@ -512,7 +581,7 @@ mp_status mp_solve_host(mp_mesh *m, const double *rho_host, double *phi_host)
     if (st != MP_OK) return st;
     const size_t bytes = (size_t)m->N * sizeof(double);
     MP_TRY(cudaMemcpyAsync(m->rho_stage, rho_host, bytes, cudaMemcpyHostToDevice, m->stream));
-    st = run_solve(m, m->rho_stage, m->phi_own);
+    st = m->profiling ? run_solve(m, m->rho_stage, m->phi_own) : solve_graph(m, m->rho_stage, m->phi_own);
     if (st != MP_OK) return st;
     MP_TRY(cudaMemcpyAsync(phi_host, m->phi_own, bytes, cudaMemcpyDeviceToHost, m->stream));
     return mp_mesh_synchronize(m);
@@ -713,7 +782,8 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
                 if (k.str() == key) {
                     m->plan.ns_s = ns_s;
                     m->plan.ns_b = ns_b;
-                    m->plan.scan_warps = sw;
+                    m->plan.scan_threads = sw;
+                    drop_graph(m);
                     return MP_OK;
                 }
             }
@@ -730,7 +800,7 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
         int ns_s, ns_b, sw;
     };
     std::vector<Cand> cands;
-    const int sws[] = {4, 8, 16, 32};
+    const int sws[] = {64, 128, 256};
     if (m->eff_prec == MP_PREC_FP64) {
         for (int sw : sws) cands.push_back({base.ns_s, base.ns_b, sw});
     } else {
@@ -744,12 +814,12 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     const int saved_prof = m->profiling;
     m->profiling = 0;
     float best = FLT_MAX;
-    Cand best_c = {base.ns_s, base.ns_b, base.scan_warps};
+    Cand best_c = {base.ns_s, base.ns_b, base.scan_threads};
     mp_status st = MP_OK;
     for (const Cand &c : cands) {
         m->plan.ns_s = c.ns_s;
         m->plan.ns_b = c.ns_b;
-        m->plan.scan_warps = c.sw;
+        m->plan.scan_threads = c.sw;
         st = run_solve(m, m->rho, phi);  // warm-up
         if (st != MP_OK) break;
         cudaEventRecord(e0, m->stream);
@@ -774,7 +844,8 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     m->profiling = saved_prof;
     m->plan.ns_s = best_c.ns_s;
     m->plan.ns_b = best_c.ns_b;
-    m->plan.scan_warps = best_c.sw;
+    m->plan.scan_threads = best_c.sw;
+    drop_graph(m);
     if (st != MP_OK) {
         m->plan = base;
         return st;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <utility>
 #include <algorithm>
 #include <cstdint>
 #include <map>
@@ -28,6 +29,7 @@ struct SplitPlan {
     int Npad = 0;         // projection GEMM N: 2L+1 rounded up to 16
     int n_kc = 0;         // projection K chunks of 16 azimuthal cells
     int Kpad = 0;         // synthesis GEMM K: 2L rounded up to 16 (m >= 1 columns)
+    int ldF = 0;          // theta contraction: padded polar-cell row of F and Ith32
     int NC = 0;           // synthesis GEMM N per chunk: min(256, n_phi rounded to 16)
     int n_nc = 0;         // synthesis N chunks
     int proj_ctas = 0;    // persistent grid sizes
@@ -35,9 +37,11 @@ struct SplitPlan {
     int proj_smem = 0;    // dynamic shared memory bytes
     int synth_smem = 0;
     int ns_s = 6;         // projection: TMA stages of the density
-    int ns_b = 3;         // synthesis: table stages
-    int jblock = 0;       // synthesis: tiles of (shells x 32 polar cells) with a resident table slice
-    int scan_warps = 16;  // radial recurrences: warps (shell chunks) per block
+    int ns_b = 3;         // synthesis: table stages (when not resident)
+    int ns_a = 2;         // synthesis: A-operand stages
+    int b_resident = 0;   // synthesis: whole table held in shared memory
+    int stg_bufs = 2;     // synthesis: TMA store staging boxes per epilogue warp
+    int scan_threads = 128;  // radial recurrences: threads (shell chunks) per moment column
 };
 
 struct ProfileEntry {
@@ -67,7 +71,7 @@ struct mp_mesh {
     double *d_Iph = nullptr;   // [P][n_p]  int cos|sin(m phi) over azimuthal cells
     double *d_Iphc = nullptr;  // [P][n_p]  Iph / dphi (cell mean)
     double *d_WR = nullptr, *d_WI = nullptr;  // [L+1][n_r]
-    double *d_RR = nullptr, *d_RI = nullptr;  // [L+1][n_r]
+    double *d_GR = nullptr, *d_GI = nullptr;  // [L+1][n_r]  -(R^R, R^I) / (2 (2l+1))
     double *d_V = nullptr;     // [n_r]
 
     // moments (both paths)
@@ -84,9 +88,11 @@ struct mp_mesh {
     mp::SplitPlan plan;
     float *d_F32 = nullptr;       // [R][Npad]
     float *d_C32 = nullptr;       // [n_r][KL]
-    float *d_IthT32 = nullptr;    // [n_t][T]   Ith, transposed, float
+    float *d_Ith32 = nullptr;     // [T][ldF]   Ith, float, zero padding
     float *d_Itc32 = nullptr;     // [T][n_t]   Ith / dmu, float
     float *d_colsum = nullptr;    // [Npad]     sum_k Iph[p][k]
+    uint8_t *d_Aop = nullptr;     // synthesis A operand, bf16 terms per 128-row tile, canonical layout
+    float *d_G0 = nullptr;        // [tiles * 128] m = 0 column of the theta synthesis
     uint8_t *d_tabB = nullptr;    // projection B operand, bf16 x 3 terms, canonical layout
     uint8_t *d_tabT = nullptr;    // synthesis B operand, bf16 x 3 terms, canonical layout
     size_t tabB_chunk_bytes = 0, tabT_chunk_bytes = 0;
@@ -102,6 +108,11 @@ struct mp_mesh {
     // TMA descriptors, cached per bound pointer
     CUtensorMap tm_rho{}, tm_phi{};
     const void *tm_rho_ptr = nullptr, *tm_phi_ptr = nullptr;
+    // the solve's kernel chain as one CUDA graph (captured on g_cap for the bound buffers)
+    cudaStream_t g_cap = nullptr;
+    cudaGraph_t g_graph = nullptr;
+    cudaGraphExec_t g_exec = nullptr;
+    const void *g_rho = nullptr, *g_phi = nullptr;
 
     // profiling
     int profiling = 0;
@@ -118,6 +129,26 @@ namespace mp {
 mp_status set_error(mp_status st, const char *fmt, ...);
 
 // ---- tables (float64, on the device) ----
+// Launch with programmatic stream serialization: the kernel may begin while
+// the previous kernel on the stream finishes; it calls pdl_wait() (ptx.cuh)
+// before it touches anything that kernel produced.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 cudaError_t launch_tables(mp_mesh *m);
 cudaError_t launch_split_tables(mp_mesh *m);
 

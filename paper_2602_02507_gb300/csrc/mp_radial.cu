@@ -8,10 +8,15 @@
 // where WR = Delta(r^3/3) (R^R)_i and WI = Delta(r^3/3) (R^I)_i are the shell
 // integrals.  Cell-centre moments are the edge means (linear interpolation to
 // the coordinate midpoint), and Eq. (Solution) gives, per shell and moment,
-//   C[i][q] = -(Delta_m / (2l+1)) [ (R^R)_i Mbar^I + (R^I)_i Mbar^R ].
+//   C[i][q] = -(Delta_m / (2l+1)) [ (R^R)_i Mbar^I + (R^I)_i Mbar^R ]
+//           = (Delta_m / 2) [ GR_i (MI_i + MI_{i+1}) + GI_i (MR_i + MR_{i+1}) ]
+// with the tables GR, GI = -(R^R, R^I) / (2 (2l+1)) and Delta_m / 2 = 1 or 2
+// (a doubling, exact).  The float64 pipe is narrow on this part, so the scans
+// keep float64 operations to the recurrences themselves.
 // A shell touching r = 0 uses, for l >= 2, the exact own-shell value
 // 6 r_1^2 / (5 (l+3)) A[0][q] in place of the divergent midpoint split.
 #include "mp_internal.h"
+#include "ptx.cuh"
 
 namespace mp {
 
@@ -54,12 +59,13 @@ __device__ __forceinline__ void block_exclusive_scans(double xf, double xb, doub
 // One block per moment column q; thread t owns shells [t*chunk, (t+1)*chunk).
 template <int NT>
 __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const double *__restrict__ WR,
-                                             const double *__restrict__ WI, const double *__restrict__ RR,
-                                             const double *__restrict__ RI, double *__restrict__ MR,
+                                             const double *__restrict__ WI, const double *__restrict__ GR,
+                                             const double *__restrict__ GI, double *__restrict__ MR,
                                              double *__restrict__ MI, double *__restrict__ C,
                                              float *__restrict__ C32, int n_r, int KL, int origin, double r1sq)
 {
     __shared__ double wt[2][NT / 32];
+    pdl_wait();  // A comes from the previous kernel
     const int q = blockIdx.x;
     int l = (int)sqrtf((float)q);
     while (l * l > q) --l;
@@ -88,7 +94,6 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
         MI[(size_t)n_r * KL + q] = mi;
     }
     // inward: edges i1-1 .. i0 and the coefficients of every shell of the chunk
-    const double half_pre = -0.5 * ((m == 0) ? 1.0 : 2.0) / (2.0 * l + 1.0);
     for (int i = i1 - 1; i >= i0; --i) {
         const double a = A[(size_t)i * KL + q];
         const double mi_hi = mi;
@@ -98,248 +103,368 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
         const double mr_hi = fma(wr[i], a, mr_lo);
         double c;
         if (origin && i == 0 && l >= 2) {
+            // the own-shell value 6 r_1^2 / (5 (l+3)) A[0][q] replaces the divergent midpoint split
             const double sself = 6.0 * r1sq / (5.0 * (l + 3.0));
-            c = 2.0 * half_pre * (RR[(size_t)l * n_r] * mi_hi + sself * a);
+            c = 2.0 * (GR[(size_t)l * n_r] * mi_hi + (-0.5 / (2.0 * l + 1.0)) * sself * a);
         } else {
-            c = half_pre * (RR[(size_t)l * n_r + i] * (mi + mi_hi) + RI[(size_t)l * n_r + i] * (mr_lo + mr_hi));
+            c = fma(GI[(size_t)l * n_r + i], mr_lo + mr_hi, GR[(size_t)l * n_r + i] * (mi + mi_hi));
         }
+        if (m > 0) c += c;
         C[(size_t)i * KL + q] = c;
-        if (C32) C32[(size_t)i * KL + q] = (float)c;
+        if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(c);
     }
 }
 
-// Split path, theta part of step (a): A[i][q] = 4 pi G sum_j Ith[t][j] F[i n_t + j][p]
-// in float32 with compensated (Kahan) summation.  Block (i, g) handles shell i
-// and moments [g * 256 QPT, (g+1) * 256 QPT).  The shell's F rows and the
-// matching table rows pass through shared memory in chunks of JC polar cells;
-// each thread owns QPT moments and keeps two Kahan streams per moment (even and
-// odd polar cells), merged in float64 at the end.
-template <int QPT>
-__global__ void __launch_bounds__(256) k32_theta(const float *__restrict__ F, const float *__restrict__ IthT,
-                                                 double *__restrict__ A, int n_t, int KL, int T, int Npad, int JC,
-                                                 double scale)
+// Same recurrences with each thread's chunk of CH shells held in registers
+// (moments, weights and edge values are loaded once, all loads up front).
+template <int NT, int CH>
+__global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, const double *__restrict__ WR,
+                                                 const double *__restrict__ WI, const double *__restrict__ GR,
+                                                 const double *__restrict__ GI, double *__restrict__ MR,
+                                                 double *__restrict__ MI, double *__restrict__ C,
+                                                 float *__restrict__ C32, int n_r, int KL, int origin, double r1sq)
 {
-    extern __shared__ float smem_t[];
-    float *sF = smem_t;                       // [JC][Npad]
-    float *sT = smem_t + (size_t)JC * Npad;   // [JC][T]
+    __shared__ double wt[2][NT / 32];
+    pdl_wait();  // A comes from the previous kernel
+    const int q = blockIdx.x;
+    int l = (int)sqrtf((float)q);
+    while (l * l > q) --l;
+    while ((l + 1) * (l + 1) <= q) ++l;
+    const int p = q - l * l;
+    const int m = pcol_m(p);
+    const int i0 = (int)threadIdx.x * CH;
+    const double *wr = WR + (size_t)l * n_r;
+    const double *wi = WI + (size_t)l * n_r;
+    const double *gr = GR + (size_t)l * n_r;
+    const double *gi = GI + (size_t)l * n_r;
+    double a[CH], w1[CH], w2[CH], g1[CH], g2[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        const int i = i0 + k;
+        const bool in = i < n_r;
+        a[k] = in ? A[(size_t)i * KL + q] : 0.0;
+        w1[k] = in ? wr[i] : 0.0;
+        w2[k] = in ? wi[i] : 0.0;
+        g1[k] = in ? gr[i] : 0.0;
+        g2[k] = in ? gi[i] : 0.0;
+    }
+    double sR = 0.0, sI = 0.0;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        sR = fma(w1[k], a[k], sR);
+        sI = fma(w2[k], a[k], sI);
+    }
+    double mr0, mi0;
+    block_exclusive_scans<NT>(sR, sI, mr0, mi0, wt);
+    double er[CH + 1], ei[CH + 1];
+    er[0] = mr0;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) er[k + 1] = fma(w1[k], a[k], er[k]);
+    ei[CH] = mi0;
+#pragma unroll
+    for (int k = CH - 1; k >= 0; --k) ei[k] = fma(w2[k], a[k], ei[k + 1]);
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        const int i = i0 + k;
+        if (i < n_r) {
+            MR[(size_t)i * KL + q] = er[k];
+            MI[(size_t)i * KL + q] = ei[k];
+            double c;
+            if (origin && i == 0 && l >= 2) {
+                // the own-shell value 6 r_1^2 / (5 (l+3)) A[0][q] replaces the divergent midpoint split
+                const double sself = 6.0 * r1sq / (5.0 * (l + 3.0));
+                c = 2.0 * (g1[k] * ei[k + 1] + (-0.5 / (2.0 * l + 1.0)) * sself * a[k]);
+            } else {
+                c = fma(g2[k], er[k] + er[k + 1], g1[k] * (ei[k] + ei[k + 1]));
+            }
+            if (m > 0) c += c;
+            C[(size_t)i * KL + q] = c;
+            if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(c);
+        }
+    }
+    if (threadIdx.x == NT - 1) {
+        // the last thread's chunk ends at or beyond the last shell: its final values are the totals
+        MR[(size_t)n_r * KL + q] = er[CH];
+        MI[(size_t)n_r * KL + q] = ei[CH];
+    }
+}
+
+// Split path, theta part of step (a):
+//   A[i][q] = 4 pi G sum_j Ith[t(l,m)][j] F[i][p][j],   q = l^2 + p, m = m(p)
+// F holds each shell as P rows of polar cells ([n_r][P][ldF]; ldF = n_t rounded
+// up to a multiple of four, plus four; padding is zero, as in the table Ith32
+// [T][ldF]).
+//
+// Persistent blocks (one per SM) keep the table in shared memory (one bulk
+// copy) and take one shell per pass, double-buffered: the next shell's rows
+// arrive by bulk copy while the block works on the current one.  Work item
+// (m, l0) covers order m, degrees l0 and l0 + 1, cos and sin: per four polar
+// cells two table float4s and two F float4s feed sixteen multiply-adds.  The
+// polar cells of an item are dealt round-robin (in float4 units) to JS = 2^jsh
+// adjacent lanes; with ldF / 4 odd and JS = 8 the eight lanes of a
+// shared-memory phase read eight different banks.  Terms are summed in float32
+// over blocks of eight cells, block sums with Kahan compensation, and the lane
+// partials are added by shuffles.  Every wait is bounded; after a failed wait
+// the block drains its own copies (bounded) and returns.
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc)
+{
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, acc))));
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Items (m, l0 = m, m + 2, ...) of order m come in ceil((L + 1 - m) / 2).
+__device__ __forceinline__ short2 theta_item(int k, int L)
+{
+    int m = 0;
+    for (;; ++m) {
+        const int np = (L + 2 - m) / 2;
+        if (k < np) break;
+        k -= np;
+    }
+    return make_short2((short)m, (short)(m + 2 * k));
+}
+
+__global__ void __launch_bounds__(1024, 1) k32_theta_pipe(const float *__restrict__ F, const float *__restrict__ Ith,
+                                                          double *__restrict__ A, int *err, int n_r, int n_t, int L,
+                                                          int KL, int P, int ldF, int n_items, int jsh,
+                                                          uint32_t tab_bytes, double scale)
+{
+    extern __shared__ __align__(16) uint8_t smem_tp[];
+    const size_t shell_floats = (size_t)P * ldF;
+    const uint32_t shell_bytes = (uint32_t)(shell_floats * 4);
+    float *sT = reinterpret_cast<float *>(smem_tp);                                  // [T][ldF]
+    float *sF = reinterpret_cast<float *>(smem_tp + tab_bytes);                      // [2][P][ldF]
+    short2 *sItem = reinterpret_cast<short2 *>(sF + 2 * shell_floats);               // [n_items]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sItem + ((n_items + 1) & ~1));     // table, rows[2]
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 3);
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+    const int JS = 1 << jsh;
+    if (tid == 0) {
+        for (int b = 0; b < 3; ++b) mbar_init(smem_u32(&bars[b]), 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    for (int it = tid; it < n_items; it += nthr) sItem[it] = theta_item(it, L);
+    __syncthreads();
+    int issued[2] = {0, 0};  // bulk copies issued per row buffer (thread 0)
+    auto issue = [&](int i, int buf) {
+        mbar_arrive_expect_tx(smem_u32(&bars[1 + buf]), shell_bytes);
+        bulk_load(smem_u32(sF + (size_t)buf * shell_floats), F + (size_t)i * shell_floats, shell_bytes,
+                  smem_u32(&bars[1 + buf]));
+        ++issued[buf];
+    };
+    if (tid == 0) {
+        mbar_arrive_expect_tx(smem_u32(&bars[0]), tab_bytes);
+        bulk_load(smem_u32(sT), Ith, tab_bytes, smem_u32(&bars[0]));
+    }
+    // the table copy overlaps the previous kernel's tail; F rows only after it completed
+    pdl_trigger();
+    pdl_wait();
+    if (tid == 0)
+        for (int b = 0; b < 2; ++b)
+            if ((int)blockIdx.x + b * (int)gridDim.x < n_r) issue(blockIdx.x + b * gridDim.x, b);
+    const bool table_ok = mbar_wait(smem_u32(&bars[0]), 0, abort_flag, err);
+    bool ok = table_ok;
+    int consumed[2] = {0, 0};
+    const int nq = (n_t + 3) / 4;  // float4 units of polar cells per row
+    const int n_work = n_items << jsh;
+
+    // one item's lane partial for shell buffer fb, summed over the JS lanes, written by lane js = 0
+    auto item = [&](const float *fb, double *Ai, int w) {
+        const int js = w & (JS - 1);
+        const bool act = w < n_work;
+        float part[4] = {0.f, 0.f, 0.f, 0.f};
+        int m = 0, l0 = 0;
+        if (act) {
+            const short2 itm = sItem[w >> jsh];
+            m = itm.x;
+            l0 = itm.y;
+            const int pc = (m == 0) ? 0 : 2 * m - 1, ps = (m == 0) ? 0 : 2 * m;
+            const float4 *fc = reinterpret_cast<const float4 *>(fb + (size_t)pc * ldF);
+            const float4 *fs = reinterpret_cast<const float4 *>(fb + (size_t)ps * ldF);
+            const float4 *t0 = reinterpret_cast<const float4 *>(sT + (size_t)tri(l0, m) * ldF);
+            const float4 *t1 = reinterpret_cast<const float4 *>(sT + (size_t)tri(min(l0 + 1, L), m) * ldF);
+            float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int u = js; u < nq; u += 2 * JS) {
+                const float4 x0 = fc[u], y0 = fs[u], a0 = t0[u], b0 = t1[u];
+                float blk[4];
+                blk[0] = dot4(a0, x0, 0.f);
+                blk[1] = dot4(a0, y0, 0.f);
+                blk[2] = dot4(b0, x0, 0.f);
+                blk[3] = dot4(b0, y0, 0.f);
+                if (u + JS < nq) {
+                    const float4 x1 = fc[u + JS], y1 = fs[u + JS], a1 = t0[u + JS], b1 = t1[u + JS];
+                    blk[0] = dot4(a1, x1, blk[0]);
+                    blk[1] = dot4(a1, y1, blk[1]);
+                    blk[2] = dot4(b1, x1, blk[2]);
+                    blk[3] = dot4(b1, y1, blk[3]);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) kahan_add(s[e], c[e], blk[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) part[e] = s[e] - c[e];
+        }
+        for (int o = 1; o < JS; o <<= 1)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) part[e] += __shfl_xor_sync(0xFFFFFFFFu, part[e], o);
+        if (act && js == 0) {
+            const int pc = (m == 0) ? 0 : 2 * m - 1;
+            Ai[l0 * l0 + pc] = scale * f32_to_f64_alu(part[0]);
+            if (m > 0) Ai[l0 * l0 + pc + 1] = scale * f32_to_f64_alu(part[1]);
+            if (l0 + 1 <= L) {
+                Ai[(l0 + 1) * (l0 + 1) + pc] = scale * f32_to_f64_alu(part[2]);
+                if (m > 0) Ai[(l0 + 1) * (l0 + 1) + pc + 1] = scale * f32_to_f64_alu(part[3]);
+            }
+        }
+    };
+
+    int k = 0;
+    for (int i = blockIdx.x; i < n_r; i += gridDim.x, ++k) {
+        const int b = k & 1;
+        if (ok) ok = mbar_wait(smem_u32(&bars[1 + b]), (uint32_t)(k >> 1) & 1u, abort_flag, err);
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        ++consumed[b];
+        const float *fb = sF + (size_t)b * shell_floats;
+        // whole warps run the loop together (the lane partials meet by shuffles)
+        for (int wb = tid - lane; wb < n_work; wb += nthr) item(fb, A + (size_t)i * KL, wb + lane);
+        __syncthreads();  // buffer b consumed
+        if (tid == 0 && i + 2 * (int)gridDim.x < n_r) issue(i + 2 * gridDim.x, b);
+    }
+    if (!ok && tid == 0) {
+        // drain this block's copies still in flight (bounded waits)
+        const long long t0 = clock64();
+        if (!table_ok)
+            while (!mbar_try_wait(smem_u32(&bars[0]), 0) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
+            }
+        for (int b = 0; b < 2; ++b) {
+            if (issued[b] > consumed[b]) {
+                const uint32_t par = (uint32_t)(issued[b] - 1) & 1u;
+                const long long t1 = clock64();
+                while (!mbar_try_wait(smem_u32(&bars[1 + b]), par) && clock64() - t1 < MP_WAIT_BUDGET_CYCLES) {
+                }
+            }
+        }
+    }
+}
+
+// Same sums for meshes whose table and rows do not fit in shared memory: block
+// i, thread per (l, m) pair, table and rows read through L1.
+__global__ void __launch_bounds__(256) k32_theta_direct(const float *__restrict__ F, const float *__restrict__ Ith,
+                                                        double *__restrict__ A, int n_t, int L, int KL, int T, int P,
+                                                        int ldF, double scale)
+{
     const int i = blockIdx.x;
-    const int qbase = blockIdx.y * blockDim.x * QPT;
-    int tq[QPT], pq[QPT];
-    float s0[QPT], c0[QPT], s1[QPT], c1[QPT];
-#pragma unroll
-    for (int u = 0; u < QPT; ++u) {
-        const int q = qbase + threadIdx.x + u * blockDim.x;
-        int l = (int)sqrtf((float)q);
-        while (l * l > q) --l;
-        while ((l + 1) * (l + 1) <= q) ++l;
-        const int p = q - l * l;
-        tq[u] = (q < KL) ? tri(l, pcol_m(p)) : 0;
-        pq[u] = (q < KL) ? p : 0;
-        s0[u] = c0[u] = s1[u] = c1[u] = 0.0f;
-    }
-    const float *Fi = F + (size_t)i * n_t * Npad;
-    for (int j0 = 0; j0 < n_t; j0 += JC) {
-        const int nj = min(JC, n_t - j0);
-        __syncthreads();
-        {
-            const float4 *src = reinterpret_cast<const float4 *>(Fi + (size_t)j0 * Npad);
-            float4 *dst = reinterpret_cast<float4 *>(sF);
-            for (int e = threadIdx.x; e < nj * Npad / 4; e += blockDim.x) dst[e] = src[e];
-            const float *tsrc = IthT + (size_t)j0 * T;
-            for (int e = threadIdx.x; e < nj * T; e += blockDim.x) sT[e] = __ldg(tsrc + e);
-        }
-        __syncthreads();
-        int j = 0;
-        for (; j + 1 < nj; j += 2) {
-            const float *ta = sT + (size_t)j * T, *tb = ta + T;
-            const float *fa = sF + j * Npad, *fb = fa + Npad;
-#pragma unroll
-            for (int u = 0; u < QPT; ++u) {
-                const float ya = __fmul_rn(ta[tq[u]], fa[pq[u]]) - c0[u];
-                const float yb = __fmul_rn(tb[tq[u]], fb[pq[u]]) - c1[u];
-                const float xa = __fadd_rn(s0[u], ya);
-                const float xb = __fadd_rn(s1[u], yb);
-                c0[u] = __fsub_rn(__fsub_rn(xa, s0[u]), ya);
-                c1[u] = __fsub_rn(__fsub_rn(xb, s1[u]), yb);
-                s0[u] = xa;
-                s1[u] = xb;
+    const float *fr = F + (size_t)i * P * ldF;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        int l = 0;
+        while ((l + 1) * (l + 2) / 2 <= t) ++l;
+        const int m = t - l * (l + 1) / 2;
+        const int pc = (m == 0) ? 0 : 2 * m - 1;
+        const float *tr = Ith + (size_t)t * ldF, *fc = fr + (size_t)pc * ldF, *fs = fr + (size_t)(pc + 1) * ldF;
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+        for (int j0 = 0; j0 < n_t; j0 += 8) {
+            float b0 = 0.f, b1 = 0.f;
+            for (int j = j0; j < min(n_t, j0 + 8); ++j) {
+                const float w = __ldg(tr + j);
+                b0 = fmaf(w, __ldg(fc + j), b0);
+                if (m > 0) b1 = fmaf(w, __ldg(fs + j), b1);
             }
+            kahan_add(s0, c0, b0);
+            kahan_add(s1, c1, b1);
         }
-        if (j < nj) {
-            const float *ta = sT + (size_t)j * T;
-            const float *fa = sF + j * Npad;
-#pragma unroll
-            for (int u = 0; u < QPT; ++u) {
-                const float ya = __fmul_rn(ta[tq[u]], fa[pq[u]]) - c0[u];
-                const float xa = __fadd_rn(s0[u], ya);
-                c0[u] = __fsub_rn(__fsub_rn(xa, s0[u]), ya);
-                s0[u] = xa;
-            }
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < QPT; ++u) {
-        const int q = qbase + threadIdx.x + u * blockDim.x;
-        if (q < KL)
-            A[(size_t)i * KL + q] = scale * (((double)s0[u] - (double)c0[u]) + ((double)s1[u] - (double)c1[u]));
-    }
-}
-
-// Same contraction, persistent: the whole table IthT [n_t][T] stays in shared
-// memory and each block walks shells i = blockIdx.x, blockIdx.x + gridDim.x, ...
-// staging one shell's F rows at a time (used when the table fits).  Each thread
-// owns moments q = threadIdx.x + k blockDim.x; terms are summed in float32 in
-// blocks of eight polar cells and the block sums are added with Kahan
-// compensation.
-__global__ void __launch_bounds__(1024) k32_theta_res(const float *__restrict__ F, const float *__restrict__ IthT,
-                                                      double *__restrict__ A, int n_r, int n_t, int KL, int T,
-                                                      int Npad, double scale)
-{
-    extern __shared__ float smem_t[];
-    float *sT = smem_t;                        // [n_t][T]
-    float *sF = smem_t + (((size_t)n_t * T + 3) & ~(size_t)3);  // [n_t][Npad]
-    const int nT = n_t * T;
-    {
-        const float4 *src = reinterpret_cast<const float4 *>(IthT);
-        float4 *dst = reinterpret_cast<float4 *>(sT);
-        const int n4 = nT / 4;
-        for (int e0 = threadIdx.x; e0 < n4; e0 += 8 * blockDim.x) {
-            float4 v[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int e = e0 + k * blockDim.x;
-                if (e < n4) v[k] = __ldg(src + e);
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int e = e0 + k * blockDim.x;
-                if (e < n4) dst[e] = v[k];
-            }
-        }
-        for (int e = n4 * 4 + threadIdx.x; e < nT; e += blockDim.x) sT[e] = __ldg(IthT + e);
-    }
-    const int n4F = n_t * Npad / 4;
-    for (int i = blockIdx.x; i < n_r; i += gridDim.x) {
-        __syncthreads();  // previous shell's rows fully read (and, the first time, the table stored)
-        {
-            const float4 *src = reinterpret_cast<const float4 *>(F + (size_t)i * n_t * Npad);
-            float4 *dst = reinterpret_cast<float4 *>(sF);
-            for (int e0 = threadIdx.x; e0 < n4F; e0 += 8 * blockDim.x) {
-                float4 v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int e = e0 + k * blockDim.x;
-                    if (e < n4F) v[k] = __ldcs(src + e);
-                }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int e = e0 + k * blockDim.x;
-                    if (e < n4F) dst[e] = v[k];
-                }
-            }
-        }
-        __syncthreads();
-        for (int q = threadIdx.x; q < KL; q += blockDim.x) {
-            int l = (int)sqrtf((float)q);
-            while (l * l > q) --l;
-            while ((l + 1) * (l + 1) <= q) ++l;
-            const int p = q - l * l;
-            const float *tcol = sT + tri(l, pcol_m(p));
-            const float *fcol = sF + p;
-            float s = 0.0f, c = 0.0f;
-            int j = 0;
-            for (; j + 8 <= n_t; j += 8) {
-                float b0 = 0.0f, b1 = 0.0f;
-#pragma unroll
-                for (int jj = 0; jj < 8; jj += 2) {
-                    b0 = fmaf(tcol[(size_t)(j + jj) * T], fcol[(j + jj) * Npad], b0);
-                    b1 = fmaf(tcol[(size_t)(j + jj + 1) * T], fcol[(j + jj + 1) * Npad], b1);
-                }
-                const float y = (b0 + b1) - c;
-                const float t = s + y;
-                c = (t - s) - y;
-                s = t;
-            }
-            float b0 = 0.0f;
-            for (; j < n_t; ++j) b0 = fmaf(tcol[(size_t)j * T], fcol[j * Npad], b0);
-            const float y = b0 - c;
-            const float t = s + y;
-            c = (t - s) - y;
-            s = t;
-            A[(size_t)i * KL + q] = scale * ((double)s - (double)c);
-        }
+        A[(size_t)i * KL + l * l + pc] = scale * (double)(s0 - c0);
+        if (m > 0) A[(size_t)i * KL + l * l + pc + 1] = scale * (double)(s1 - c1);
     }
 }
 
 }  // namespace
+
+template <int NT, int CH>
+static void scan_reg_launch(mp_mesh *m, int want_f32, double r1sq)
+{
+    launch_pdl(k_scan_reg<NT, CH>, dim3(m->KL), dim3(NT), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
+               m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, m->n_r, m->KL, m->origin, r1sq);
+}
+
+// Shells per thread CH for NT threads per moment column; false when n_r > 16 NT.
+template <int NT>
+static bool scan_reg_dispatch(mp_mesh *m, int want_f32, double r1sq)
+{
+    const int ch = (m->n_r + NT - 1) / NT;
+    if (ch <= 1)
+        scan_reg_launch<NT, 1>(m, want_f32, r1sq);
+    else if (ch <= 2)
+        scan_reg_launch<NT, 2>(m, want_f32, r1sq);
+    else if (ch <= 4)
+        scan_reg_launch<NT, 4>(m, want_f32, r1sq);
+    else if (ch <= 8)
+        scan_reg_launch<NT, 8>(m, want_f32, r1sq);
+    else if (ch <= 16)
+        scan_reg_launch<NT, 16>(m, want_f32, r1sq);
+    else
+        return false;
+    return true;
+}
 
 cudaError_t launch_scan(mp_mesh *m, int want_f32)
 {
     const double r1sq = m->h_r[1] * m->h_r[1];
     cudaEvent_t ev;
     prof_begin(m, "radial_scan", &ev);
-    k_scan<kScanThreads><<<m->KL, kScanThreads, 0, m->stream>>>(m->d_A, m->d_WR, m->d_WI, m->d_RR, m->d_RI, m->d_MR,
-                                                                m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr,
-                                                                m->n_r, m->KL, m->origin, r1sq);
+    bool done;
+    switch (m->plan.scan_threads) {
+    case 64: done = scan_reg_dispatch<64>(m, want_f32, r1sq); break;
+    case 256: done = scan_reg_dispatch<256>(m, want_f32, r1sq); break;
+    default: done = scan_reg_dispatch<kScanThreads>(m, want_f32, r1sq); break;
+    }
+    if (!done)
+        k_scan<kScanThreads><<<m->KL, kScanThreads, 0, m->stream>>>(m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
+                                                                    m->d_MR, m->d_MI, m->d_C,
+                                                                    want_f32 ? m->d_C32 : nullptr, m->n_r, m->KL,
+                                                                    m->origin, r1sq);
     prof_end(m, "radial_scan", ev);
     return cudaGetLastError();
 }
 
-template <int QPT>
-static void theta_launch(mp_mesh *m, int JC, size_t smem, double scale)
-{
-    const dim3 grid(m->n_r, (m->KL + 256 * QPT - 1) / (256 * QPT));
-    k32_theta<QPT><<<grid, 256, smem, m->stream>>>(m->d_F32, m->d_IthT32, m->d_A, m->n_t, m->KL, m->T,
-                                                   m->plan.Npad, JC, scale);
-}
-
-static void theta_res_launch(mp_mesh *m, size_t smem, double scale)
-{
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k32_theta_res, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
-        attr_set = true;
-    }
-    const int threads = std::min(1024, 32 * ((m->KL + 31) / 32));
-    const int grid = std::min(m->n_r, 2 * m->num_sms);
-    k32_theta_res<<<grid, threads, smem, m->stream>>>(m->d_F32, m->d_IthT32, m->d_A, m->n_r, m->n_t, m->KL, m->T,
-                                                      m->plan.Npad, scale);
-}
 
 cudaError_t launch_split_theta(mp_mesh *m)
 {
     constexpr double kFourPi = 12.566370614359172954;
-    const int Npad = m->plan.Npad;
-    // resident table: two blocks per SM when table + one shell's rows fit in 112 KB
-    const size_t res_smem = ((((size_t)m->n_t * m->T + 3) & ~(size_t)3) + (size_t)m->n_t * Npad) * sizeof(float);
-    if (res_smem <= 112 * 1024) {
-        cudaEvent_t ev;
-        prof_begin(m, "split_theta_contract", &ev);
-        theta_res_launch(m, res_smem, kFourPi * m->G);
-        prof_end(m, "split_theta_contract", ev);
-        return cudaGetLastError();
-    }
-    // polar cells per chunk: F rows plus table rows within 48 KB of shared memory
-    const int JC = std::max(1, std::min(m->n_t, (48 * 1024) / ((Npad + m->T) * 4)));
-    const size_t smem = (size_t)JC * (Npad + m->T) * sizeof(float);
-    if (smem > 48 * 1024) {
-        cudaFuncSetAttribute(k32_theta<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k32_theta<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k32_theta<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k32_theta<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
-    const int qpt = (m->KL + 255) / 256;
-    const double scale = kFourPi * m->G;
+    const int ldF = m->plan.ldF, L = m->L, P = m->P;
+    const uint32_t tab_bytes = (uint32_t)((size_t)m->T * ldF * 4);
+    int n_items = 0;
+    for (int mm = 0; mm <= L; ++mm) n_items += (L + 2 - mm) / 2;
+    // lanes per item: eight when a row has enough float4 units to go round
+    const int nq = (m->n_t + 3) / 4;
+    const int jsh = nq >= 16 ? 3 : (nq >= 8 ? 2 : (nq >= 4 ? 1 : 0));
+    const size_t smem = (size_t)tab_bytes + 2 * (size_t)P * ldF * 4 + (size_t)((n_items + 1) & ~1) * 4 + 3 * 8 + 16;
     cudaEvent_t ev;
     prof_begin(m, "split_theta_contract", &ev);
-    if (qpt <= 1)
-        theta_launch<1>(m, JC, smem, scale);
-    else if (qpt <= 2)
-        theta_launch<2>(m, JC, smem, scale);
-    else if (qpt <= 4)
-        theta_launch<4>(m, JC, smem, scale);
-    else
-        theta_launch<8>(m, JC, smem, scale);
+    if (smem <= 200 * 1024) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k32_theta_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr_set = true;
+        }
+        const int threads = std::min(1024, 32 * (((n_items << jsh) + 31) / 32));
+        const int grid = std::min(m->n_r, m->num_sms);
+        launch_pdl(k32_theta_pipe, dim3(grid), dim3(threads), smem, m->stream, m->d_F32, m->d_Ith32, m->d_A, m->d_err,
+                   m->n_r, m->n_t, L, m->KL, P, ldF, n_items, jsh, tab_bytes, kFourPi * m->G);
+    } else {
+        k32_theta_direct<<<m->n_r, 256, 0, m->stream>>>(m->d_F32, m->d_Ith32, m->d_A, m->n_t, L, m->KL, m->T, P, ldF,
+                                                        kFourPi * m->G);
+    }
     prof_end(m, "split_theta_contract", ev);
     return cudaGetLastError();
 }

@@ -21,8 +21,8 @@
 // leave through TMA stores.
 //
 // Roles per CTA (persistent, one CTA per SM): warp 0 issues TMA / bulk copies,
-// warp 1 owns tensor memory and issues the MMAs, warps 2..9 convert and run
-// the epilogues.  Every mbarrier wait is bounded (ptx.cuh).
+// warp 1 owns tensor memory and issues the MMAs, the other warps convert and
+// run the epilogues.  Every mbarrier wait is bounded (ptx.cuh).
 #include <cstdio>
 
 #include "mp_internal.h"
@@ -33,8 +33,6 @@ namespace mp {
 namespace {
 
 constexpr int kBM = 128;      // rows per tile (UMMA M)
-constexpr int kConvWarps = 8; // converter / epilogue warps
-constexpr int kThreads = (2 + kConvWarps) * 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // bf16 product terms (a_term, b_term) accumulated per K step.
@@ -74,18 +72,38 @@ struct Ring {
     }
 };
 
+// Chunk order of a tile: a rotation by a tile-dependent offset, so that the SMs
+// streaming different tiles address different parts of their rows at any moment
+// (a common order sends every SM's requests to the same few memory channels).
+__device__ __forceinline__ int rotated_chunk(int it, int tile, int n)
+{
+    int k = it + (int)(((unsigned)tile * 5u) % (unsigned)n);
+    return k >= n ? k - n : k;
+}
+
 struct ProjParams {
     const uint8_t *tabB;   // [n_kc][3][Npad x 32] bf16, canonical layout
     const float *colsum;   // [Npad]
-    float *F;              // [R][Npad]
+    const double *rho;     // [R][n_p], read directly only for the row reference values
+    float *F;              // [n_r][P][ldF]: per shell, the P columns as rows of polar cells
     int *err;
     long long R;
     int n_p, n_kc, Npad, n_tiles, ns_s, ns_o;
-    uint32_t bchunk;       // bytes of one B chunk (3 terms)
+    int n_t, P, ldF;
+    uint32_t bchunk;       // bytes of one B chunk in the table (3 terms)
+    uint32_t bload;        // bytes of the terms the products read (a prefix of the chunk)
 };
 
+// Converter warps: two groups of kGroupWarps; group g converts the chunks whose
+// CTA-wide sequence number c has c % 2 == g, so that each SM sub-partition holds
+// four converter warps (their integer conversion chains hide each other's latency).
+constexpr int kGroupWarps = 8;
+constexpr int kProjConvWarps = 2 * kGroupWarps;
+constexpr int kProjThreads = (2 + kProjConvWarps) * 32;
+
 template <int A_TERMS, int NPROD>
-__global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__ CUtensorMap tmS, const ProjParams prm)
+__global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_constant__ CUtensorMap tmS,
+                                                             const ProjParams prm)
 {
     using namespace proj;
     extern __shared__ uint8_t smem_raw[];
@@ -93,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
     const int NS_S = prm.ns_s, NS_O = prm.ns_o;
     uint8_t *sS = smem;
     uint8_t *sB = sS + (size_t)NS_S * S_BYTES;
-    uint8_t *sA = sB + (size_t)NS_S * prm.bchunk;
+    uint8_t *sA = sB + (size_t)NS_S * prm.bload;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sA + (size_t)NS_O * A_TERMS * A_TERM_BYTES);
     uint64_t *s_full = bars, *s_empty = bars + NS_S;
     uint64_t *b_full = bars + 2 * NS_S, *b_empty = b_full + NS_S;
@@ -110,17 +128,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS_S; ++s) {
             mbar_init(smem_u32(&s_full[s]), 1);
-            mbar_init(smem_u32(&s_empty[s]), kConvWarps);  // density stages: free once converted
+            mbar_init(smem_u32(&s_empty[s]), kGroupWarps);  // density stages: free once converted
             mbar_init(smem_u32(&b_full[s]), 1);
-            mbar_init(smem_u32(&b_empty[s]), 1);           // table stages: free once the MMAs read them
+            mbar_init(smem_u32(&b_empty[s]), 1);            // table stages: free once the MMAs read them
         }
         for (int o = 0; o < NS_O; ++o) {
-            mbar_init(smem_u32(&o_full[o]), kConvWarps);
+            mbar_init(smem_u32(&o_full[o]), kGroupWarps);
             mbar_init(smem_u32(&o_empty[o]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&acc_full[b]), 1);
-            mbar_init(smem_u32(&acc_empty[b]), kConvWarps);
+            mbar_init(smem_u32(&acc_empty[b]), kProjConvWarps);
         }
         mbar_init(smem_u32(drain), 1);
         *abort_flag = 0;
@@ -134,6 +152,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
+    // barrier set-up and tensor memory overlap the previous kernel's tail; the density and
+    // the outputs are touched only after the previous kernel has completed
+    pdl_trigger();
+    pdl_wait();
 
     if (warp == 0) {
         // ---------------- producer: two TMA boxes of rho, and the table chunk on its own ring
@@ -142,7 +164,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
             Ring rs;
             int issued = 0;
             for (int tile = blockIdx.x; tile < prm.n_tiles && !*abort_flag; tile += gridDim.x) {
-                for (int kc = 0; kc < prm.n_kc; ++kc, rs.next(NS_S)) {
+                for (int it = 0; it < prm.n_kc; ++it, rs.next(NS_S)) {
+                    const int kc = rotated_chunk(it, tile, prm.n_kc);
                     if (!mbar_wait(smem_u32(&s_empty[rs.idx]), rs.phase ^ 1, abort_flag, prm.err)) break;
                     const uint32_t fb = smem_u32(&s_full[rs.idx]);
                     const bool two = kc * BK + 16 < prm.n_p;  // the second box holds cells
@@ -155,9 +178,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
                         break;
                     }
                     const uint32_t bb = smem_u32(&b_full[rs.idx]);
-                    mbar_arrive_expect_tx(bb, prm.bchunk);
-                    bulk_load(smem_u32(sB + (size_t)rs.idx * prm.bchunk), prm.tabB + (size_t)kc * prm.bchunk,
-                              prm.bchunk, bb);
+                    mbar_arrive_expect_tx(bb, prm.bload);
+                    bulk_load(smem_u32(sB + (size_t)rs.idx * prm.bload), prm.tabB + (size_t)kc * prm.bchunk,
+                              prm.bload, bb);
                     ++issued;
                 }
             }
@@ -179,6 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(kBM, Npad);
+            const uint32_t b_term = (uint32_t)Npad * (BK * 2);
             Ring rs, ro;
             int lt = 0;
             bool ok = true;
@@ -188,22 +212,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)b * acc_stride;
-                for (int kc = 0; kc < prm.n_kc; ++kc, rs.next(NS_S), ro.next(NS_O)) {
+                for (int it = 0; it < prm.n_kc; ++it, rs.next(NS_S), ro.next(NS_O)) {
                     ok = mbar_wait(smem_u32(&o_full[ro.idx]), ro.phase, abort_flag, prm.err) &&
                          mbar_wait(smem_u32(&b_full[rs.idx]), rs.phase, abort_flag, prm.err);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t a_base = smem_u32(sA + (size_t)ro.idx * A_TERMS * A_TERM_BYTES);
-                    const uint32_t b_base = smem_u32(sB + (size_t)rs.idx * prm.bchunk);
+                    const uint32_t b_base = smem_u32(sB + (size_t)rs.idx * prm.bload);
 #pragma unroll
                     for (int ks = 0; ks < BK / 16; ++ks) {
 #pragma unroll
                         for (int pi = 0; pi < NPROD; ++pi) {
                             const uint64_t ad =
                                 sdesc_noswizzle(a_base + c_prod_a[pi] * A_TERM_BYTES + ks * 256, 128, SBO);
-                            const uint64_t bd =
-                                sdesc_noswizzle(b_base + c_prod_b[pi] * Npad * (BK * 2) + ks * 256, 128, SBO);
-                            umma_bf16(d_tmem, ad, bd, idesc, (kc | ks | pi) != 0);
+                            const uint64_t bd = sdesc_noswizzle(b_base + c_prod_b[pi] * b_term + ks * 256, 128, SBO);
+                            umma_bf16(d_tmem, ad, bd, idesc, (it | ks | pi) != 0);
                         }
                     }
                     umma_commit(smem_u32(&o_empty[ro.idx]));
@@ -219,41 +242,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
         }
     } else {
         // ---------------- converters + epilogue
-        const int cw = warp - 2, qd = warp & 3, half = cw >> 2;
+        const int cw = warp - 2, grp = cw / kGroupWarps, qd = warp & 3, half = (cw >> 2) & 1;
         const int row = qd * 32 + lane;
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
-        Ring rs, ro;
         int lt = 0, prev_tile = -1;
+        long long c = 0;  // CTA-wide chunk sequence number (same order as the producer and the MMA)
         float sref = 0.0f, sref_prev = 0.0f;
         uint32_t efmax = 0;  // largest float64 exponent field seen (flags values beyond float32)
         bool ok = true;
 
+        // the accumulator of a finished tile: F = D + sref colsum, stored per shell as rows of
+        // polar cells (lanes hold consecutive cells: each store is coalesced); column groups
+        // split four ways
         auto epilogue = [&](int etile, int elt, float sr) -> bool {
             const int b = elt & 1;
             bool w_ok = warp_all(mbar_wait(smem_u32(&acc_full[b]), (elt >> 1) & 1, abort_flag, prm.err));
             if (!w_ok) return false;
             tc_fence_after();
             const long long grow = (long long)etile * kBM + row;
+            const long long ish = grow / prm.n_t;
+            float *fdst = prm.F + (size_t)ish * prm.P * prm.ldF + (grow - ish * prm.n_t);
             const int ngroups = Npad / 8;
-            for (int cg = half; cg < ngroups; cg += 2) {
+            for (int cg = 2 * grp + half; cg < ngroups && cg * 8 < prm.P; cg += 4) {
                 uint32_t v[8];
                 tmem_ld8(tmem_base + lane_base + (uint32_t)b * acc_stride + (uint32_t)(cg * 8), v);
                 tmem_ld_wait();
                 if (grow < prm.R) {
-                    const float4 c0 = *reinterpret_cast<const float4 *>(prm.colsum + cg * 8);
-                    const float4 c1 = *reinterpret_cast<const float4 *>(prm.colsum + cg * 8 + 4);
-                    float4 o0, o1;
-                    o0.x = fmaf(sr, c0.x, __uint_as_float(v[0]));
-                    o0.y = fmaf(sr, c0.y, __uint_as_float(v[1]));
-                    o0.z = fmaf(sr, c0.z, __uint_as_float(v[2]));
-                    o0.w = fmaf(sr, c0.w, __uint_as_float(v[3]));
-                    o1.x = fmaf(sr, c1.x, __uint_as_float(v[4]));
-                    o1.y = fmaf(sr, c1.y, __uint_as_float(v[5]));
-                    o1.z = fmaf(sr, c1.z, __uint_as_float(v[6]));
-                    o1.w = fmaf(sr, c1.w, __uint_as_float(v[7]));
-                    float4 *dst = reinterpret_cast<float4 *>(prm.F + grow * Npad + cg * 8);
-                    dst[0] = o0;
-                    dst[1] = o1;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int p = cg * 8 + e;
+                        if (p < prm.P) fdst[(size_t)p * prm.ldF] = fmaf(sr, prm.colsum[p], __uint_as_float(v[e]));
+                    }
                 }
             }
             tc_fence_before();
@@ -262,32 +281,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
             return true;
         };
 
-        // this thread converts cells [16 half, 16 half + 16) of every stage: box `half`
+        // this thread converts cells [16 half, 16 half + 16) of its group's stages: box `half`
         for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ++lt) {
-            for (int kc = 0; kc < prm.n_kc; ++kc, rs.next(NS_S), ro.next(NS_O)) {
-                ok = warp_all(mbar_wait(smem_u32(&s_full[rs.idx]), rs.phase, abort_flag, prm.err));
+            // reference value of the row: its first cell, read directly (both groups need it)
+            {
+                const long long grow = (long long)tile * kBM + row;
+                uint2 v0 = make_uint2(0u, 0u);
+                if (grow < prm.R) v0 = __ldg(reinterpret_cast<const uint2 *>(prm.rho + grow * prm.n_p));
+                uint32_t e0;
+                sref = f64w_to_f32_fast(v0.x, v0.y, e0);
+            }
+            for (int it = 0; it < prm.n_kc; ++it, ++c) {
+                if ((int)(c & 1) != grp) continue;
+                const int kc = rotated_chunk(it, tile, prm.n_kc);
+                const int sidx = (int)(c % NS_S), oidx = (int)(c % NS_O);
+                const uint32_t sph = (uint32_t)((c / NS_S) & 1), oph = (uint32_t)((c / NS_O) & 1);
+                ok = warp_all(mbar_wait(smem_u32(&s_full[sidx]), sph, abort_flag, prm.err));
                 if (!ok) break;
-                ok = warp_all(mbar_wait(smem_u32(&o_empty[ro.idx]), ro.phase ^ 1, abort_flag, prm.err));
+                ok = warp_all(mbar_wait(smem_u32(&o_empty[oidx]), oph ^ 1, abort_flag, prm.err));
                 if (!ok) break;
-                const uint8_t *sbox = sS + (size_t)rs.idx * S_BYTES + row * 128;
-                if (kc == 0) {
-                    const uint2 v0 = *reinterpret_cast<const uint2 *>(sbox + ((row & 7) << 4));
-                    uint32_t e0;
-                    sref = f64w_to_f32_fast(v0.x, v0.y, e0);
-                }
-                const uint8_t *srow = sbox + half * BOX_BYTES;
+                const uint8_t *srow = sS + (size_t)sidx * S_BYTES + half * BOX_BYTES + row * 128;
                 const int kfirst = kc * BK + half * 16;           // first cell of this thread's box
                 const bool full = kfirst + 16 <= prm.n_p;         // warp-uniform
                 uint32_t w0[8], w1[8], w2[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((c ^ (row & 7)) << 4));
+                for (int cc = 0; cc < 8; ++cc) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((cc ^ (row & 7)) << 4));
                     uint32_t e0, e1;
                     float x0 = f64w_to_f32_fast(v.x, v.y, e0) - sref;
                     float x1 = f64w_to_f32_fast(v.z, v.w, e1) - sref;
                     if (!full) {
                         // cells past the last azimuthal cell hold no data: zero deviation
-                        const bool in0 = kfirst + 2 * c < prm.n_p, in1 = kfirst + 2 * c + 1 < prm.n_p;
+                        const bool in0 = kfirst + 2 * cc < prm.n_p, in1 = kfirst + 2 * cc + 1 < prm.n_p;
                         x0 = in0 ? x0 : 0.0f;
                         x1 = in1 ? x1 : 0.0f;
                         e0 = in0 ? e0 : 0u;
@@ -297,12 +322,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
                     const uint32_t t0 = pack_bf16x2(x0, x1);
                     const float r0 = x0 - bf16lo_to_f32(t0), r1 = x1 - bf16hi_to_f32(t0);
                     const uint32_t t1 = pack_bf16x2(r0, r1);
-                    w0[c] = t0;
-                    w1[c] = t1;
-                    if (A_TERMS == 3) w2[c] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
+                    w0[cc] = t0;
+                    w1[cc] = t1;
+                    if (A_TERMS == 3) w2[cc] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
                 }
                 // K groups 2 half and 2 half + 1 of the [128 x 32] A tile, each term
-                uint8_t *adst = sA + (size_t)ro.idx * A_TERMS * A_TERM_BYTES + (row >> 3) * SBO + half * 256 +
+                uint8_t *adst = sA + (size_t)oidx * A_TERMS * A_TERM_BYTES + (row >> 3) * SBO + half * 256 +
                                 (row & 7) * 16;
 #pragma unroll
                 for (int kg = 0; kg < 2; ++kg) {
@@ -317,8 +342,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(smem_u32(&s_empty[rs.idx]));
-                    mbar_arrive(smem_u32(&o_full[ro.idx]));
+                    mbar_arrive(smem_u32(&s_empty[sidx]));
+                    mbar_arrive(smem_u32(&o_full[oidx]));
                 }
             }
             if (!ok) break;
@@ -340,82 +365,347 @@ __global__ void __launch_bounds__(kThreads, 1) k_proj_tc(const __grid_constant__
 }
 
 // ----------------------------------------------------------------------------
-// (d) reconstruction: theta synthesis on CUDA cores + phi synthesis on tcgen05
+// (d) reconstruction, part 1: theta synthesis on CUDA cores
+//   G[row][p] = sum_{l >= m(p)} (Ith[t(l,m)][j] / dmu_j) C[i][l^2 + p]
+// written as the bf16 terms of the phi-synthesis A operand -- already in the
+// canonical K-major layout of 128-row tiles (K = p - 1, p = 1 .. 2L) -- plus the
+// m = 0 column G[row][0] in float32.  One block per (shell, 256 polar cells);
+// the shell's coefficient row sits in shared memory, the table is read through
+// L1 (coalesced along the polar cells).
+// ----------------------------------------------------------------------------
+// Register-tiled theta synthesis for n_t % 4 == 0 with the table Itc [T][n_t]
+// resident in shared memory (persistent blocks walk the shells).  Thread
+// (qd, g): polar cells j = 4 qd .. 4 qd + 3 and, for g < Kpad/8, the eight K
+// columns p = 8 g + 1 .. 8 g + 8 (m = 4 g + 1 .. 4 g + 4, cos and sin); thread
+// g = Kpad/8 forms the m = 0 column.  Per (l, m) one float4 table read feeds
+// eight multiply-adds.
+// Persistent form (one block per SM): the table Itc [T][ldF] (rows padded with
+// zeros to ldF cells) arrives once by bulk copy and the block takes kGsS shells
+// per pass.  Work unit u of a shell holds the orders m = u and m = L + 1 - u
+// (u = 1 .. ceil(L/2); unit 0 is m = 0), so that every unit sums L + 1 terms
+// per output pair and the warps finish together.  Lane t of a unit's warp forms
+// four consecutive polar cells (one float4 table read feeds eight
+// multiply-adds).  G collects in shared memory column-major ([K][ldF]) and
+// leaves in a second pass as the bf16 terms of the canonical K-major MMA layout
+// (16-byte stores, coalesced); the m = 0 column leaves as float32.  The next
+// pass's coefficients are read into registers during the output pass.
+constexpr int kGsS = 2;   // shells per pass
+constexpr int kGsPre = 4; // coefficient registers per thread (kGsS * KL <= kGsPre * threads)
+
+template <int A_TERMS>
+__global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict__ C32, const float *__restrict__ Itc,
+                                                         uint8_t *__restrict__ Aop, float *__restrict__ G0, int *err,
+                                                         int n_r, int n_t, int L, int KL, int Kpad, int ldF,
+                                                         uint32_t tab_bytes)
+{
+    extern __shared__ __align__(16) uint8_t smem_gp[];
+    float *sI = reinterpret_cast<float *>(smem_gp);                              // [T][ldF]
+    float *sG = reinterpret_cast<float *>(smem_gp + tab_bytes);                  // [kGsS][Kpad][ldF]
+    float *sC = sG + (size_t)kGsS * Kpad * ldF;                                  // [kGsS][KL]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sC + (((size_t)kGsS * KL + 1) & ~(size_t)1));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 1);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) {
+        mbar_init(smem_u32(bar), 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(smem_u32(bar), tab_bytes);
+        bulk_load(smem_u32(sI), Itc, tab_bytes, smem_u32(bar));
+    }
+    // the table copy overlaps the previous kernel's tail; coefficients only after it completed
+    pdl_trigger();
+    pdl_wait();
+    const int U = 1 + (L + 1) / 2;      // work units per group of 128 polar cells
+    const int nq = (n_t + 3) / 4;       // float4 units of polar cells
+    const int NJ = (nq + 31) / 32;
+    const int n_work = kGsS * NJ * U * 32;
+    const int ngk = Kpad / 8;
+    const int n_out = kGsS * n_t * ngk;
+    const int n_cf = kGsS * KL;
+    const size_t a_term_bytes = (size_t)128 * Kpad * 2;
+    const int n_pass = (n_r + kGsS - 1) / kGsS;
+    // K columns past 2L never receive a term: zero once
+    for (int e = tid; e < kGsS * (Kpad - 2 * L) * ldF; e += nthr) {
+        const int kk = 2 * L + (e / ldF) % (Kpad - 2 * L), sh = e / ((Kpad - 2 * L) * ldF);
+        sG[((size_t)sh * Kpad + kk) * ldF + e % ldF] = 0.0f;
+    }
+    float cv[kGsPre];
+    auto load_coefficients = [&](int pass) {
+#pragma unroll
+        for (int k = 0; k < kGsPre; ++k) {
+            const int e = tid + k * nthr;
+            if (e < n_cf) {
+                const int i = pass * kGsS + e / KL;
+                cv[k] = (i < n_r) ? __ldg(C32 + (size_t)i * KL + e % KL) : 0.0f;
+            }
+        }
+    };
+    if ((int)blockIdx.x < n_pass) load_coefficients(blockIdx.x);
+    const bool ok = mbar_wait(smem_u32(bar), 0, abort_flag, err);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(smem_u32(bar), 0) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
+            }
+        }
+        return;
+    }
+    // compute-phase work item w = tid + r nthr: (lane, unit u, 128-cell group jg, shell slot sh)
+    auto compute = [&](int pass, int w) {
+        const int lane = w & 31;
+        int rest = w >> 5;
+        const int u = rest % U;
+        rest /= U;
+        const int jg = rest % NJ, sh = rest / NJ;
+        const int i = pass * kGsS + sh;
+        const int uq = jg * 32 + lane;  // float4 unit of polar cells
+        if (i >= n_r || uq >= nq) return;
+        const float *cf = sC + (size_t)sh * KL;
+        float *gs = sG + (size_t)sh * Kpad * ldF;
+        if (u == 0) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float *tr = sI + 4 * uq;
+            for (int l = 0; l <= L; ++l) {
+                const float c = cf[l * l];
+                const float4 t = *reinterpret_cast<const float4 *>(tr);
+                tr += (size_t)(l + 1) * ldF;  // tri(l + 1, 0) = tri(l, 0) + l + 1
+                a.x = fmaf(t.x, c, a.x);
+                a.y = fmaf(t.y, c, a.y);
+                a.z = fmaf(t.z, c, a.z);
+                a.w = fmaf(t.w, c, a.w);
+            }
+            const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (4 * uq + jj < n_t) G0[(size_t)i * n_t + 4 * uq + jj] = av[jj];
+            return;
+        }
+        for (int h = 0; h < 2; ++h) {
+            const int m = (h == 0) ? u : L + 1 - u;
+            if (h == 1 && m <= u) break;  // odd L: the middle order stands alone
+            float4 ac = make_float4(0.f, 0.f, 0.f, 0.f), as = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float *tr = sI + (size_t)tri(m, m) * ldF + 4 * uq;
+            const float *cp = cf + m * m + 2 * m - 1;  // C[i][l^2 + 2m - 1] at l = m
+            for (int l = m; l <= L; ++l) {
+                const float cc = cp[0], cs = cp[1];
+                cp += 2 * l + 1;                      // (l+1)^2 - l^2
+                const float4 t = *reinterpret_cast<const float4 *>(tr);
+                tr += (size_t)(l + 1) * ldF;          // tri(l + 1, m) = tri(l, m) + l + 1
+                ac.x = fmaf(t.x, cc, ac.x);
+                ac.y = fmaf(t.y, cc, ac.y);
+                ac.z = fmaf(t.z, cc, ac.z);
+                ac.w = fmaf(t.w, cc, ac.w);
+                as.x = fmaf(t.x, cs, as.x);
+                as.y = fmaf(t.y, cs, as.y);
+                as.z = fmaf(t.z, cs, as.z);
+                as.w = fmaf(t.w, cs, as.w);
+            }
+            *reinterpret_cast<float4 *>(gs + (size_t)(2 * m - 2) * ldF + 4 * uq) = ac;
+            *reinterpret_cast<float4 *>(gs + (size_t)(2 * m - 1) * ldF + 4 * uq) = as;
+        }
+    };
+    // output-phase item o = tid + r nthr: polar cell j = o mod n_t, (shell slot, K group) = o div n_t,
+    // advanced without divisions
+    const int dj = nthr % n_t, dsg = nthr / n_t;
+    const int j_first = tid % n_t, sg_first = tid / n_t;
+    for (int pass = blockIdx.x; pass < n_pass; pass += gridDim.x) {
+#pragma unroll
+        for (int k = 0; k < kGsPre; ++k) {
+            const int e = tid + k * nthr;
+            if (e < n_cf) sC[e] = cv[k];
+        }
+        __syncthreads();
+        for (int w = tid; w < n_work; w += nthr) compute(pass, w);
+        __syncthreads();
+        if (pass + (int)gridDim.x < n_pass) load_coefficients(pass + gridDim.x);
+        int j = j_first, sg = sg_first;
+        for (int o = tid; o < n_out; o += nthr) {
+            int sh = 0, g = sg;
+            while (g >= ngk) {
+                g -= ngk;
+                ++sh;
+            }
+            const int i = pass * kGsS + sh;
+            if (i < n_r) {
+                const float *gc = sG + ((size_t)sh * Kpad + 8 * g) * ldF + j;
+                uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float x0 = gc[(size_t)(2 * c) * ldF], x1 = gc[(size_t)(2 * c + 1) * ldF];
+                    const uint32_t t0 = pack_bf16x2(x0, x1);
+                    const float r0 = x0 - bf16lo_to_f32(t0), r1 = x1 - bf16hi_to_f32(t0);
+                    const uint32_t t1 = pack_bf16x2(r0, r1);
+                    w0[c] = t0;
+                    w1[c] = t1;
+                    if (A_TERMS == 3) w2[c] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
+                }
+                const long long row = (long long)i * n_t + j;
+                const int r = (int)(row & 127);
+                uint8_t *dst = Aop + (size_t)(row >> 7) * A_TERMS * a_term_bytes + (size_t)(r >> 3) * (Kpad * 16) +
+                               (r & 7) * 16 + g * 128;
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                *reinterpret_cast<uint4 *>(dst + a_term_bytes) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                if (A_TERMS == 3)
+                    *reinterpret_cast<uint4 *>(dst + 2 * a_term_bytes) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+            }
+            j += dj;
+            sg += dsg;
+            if (j >= n_t) {
+                j -= n_t;
+                ++sg;
+            }
+        }
+        __syncthreads();  // G columns and coefficients of this pass consumed
+    }
+}
+
+template <int A_TERMS>
+__global__ void __launch_bounds__(256) k_gsynth(const float *__restrict__ C32, const float *__restrict__ Itc,
+                                                uint8_t *__restrict__ Aop, float *__restrict__ G0, int n_t, int L,
+                                                int KL, int Kpad, int ldF)
+{
+    // block (i, y): shell i, polar cells j = y * jpb + threadIdx.y; threadIdx.x = group gi of
+    // eight K columns (p = 8 gi + 1 .. 8 gi + 8), and one extra lane group for p = 0
+    extern __shared__ float sCrow[];  // [KL]
+    const int i = blockIdx.x;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int e = tid; e < KL; e += blockDim.x * blockDim.y) sCrow[e] = C32[(size_t)i * KL + e];
+    __syncthreads();
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (j >= n_t) return;
+    const long long row = (long long)i * n_t + j;
+    const float *itab = Itc + j;
+    const int ngrp = Kpad / 8;
+    const int gi = threadIdx.x;
+    if (gi == ngrp) {
+        float g0 = 0.0f, g1 = 0.0f;
+        int l = 0;
+        for (; l + 1 <= L; l += 2) {
+            g0 = fmaf(__ldg(itab + (size_t)tri(l, 0) * ldF), sCrow[l * l], g0);
+            g1 = fmaf(__ldg(itab + (size_t)tri(l + 1, 0) * ldF), sCrow[(l + 1) * (l + 1)], g1);
+        }
+        if (l <= L) g0 = fmaf(__ldg(itab + (size_t)tri(l, 0) * ldF), sCrow[l * l], g0);
+        G0[row] = g0 + g1;
+        return;
+    }
+    if (gi > ngrp) return;
+    float gv[8];
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) {
+        const int m = 4 * gi + mm + 1;
+        float ac = 0.0f, as = 0.0f, bc = 0.0f, bs = 0.0f;
+        if (m <= L) {
+            const float *cc = sCrow + 2 * m - 1;  // C[i][l^2 + 2m - 1], C[i][l^2 + 2m]
+            int l = m;
+            for (; l + 1 <= L; l += 2) {
+                const float w0 = __ldg(itab + (size_t)tri(l, m) * ldF);
+                const float w1 = __ldg(itab + (size_t)tri(l + 1, m) * ldF);
+                ac = fmaf(w0, cc[l * l], ac);
+                as = fmaf(w0, cc[l * l + 1], as);
+                bc = fmaf(w1, cc[(l + 1) * (l + 1)], bc);
+                bs = fmaf(w1, cc[(l + 1) * (l + 1) + 1], bs);
+            }
+            if (l <= L) {
+                const float w0 = __ldg(itab + (size_t)tri(l, m) * ldF);
+                ac = fmaf(w0, cc[l * l], ac);
+                as = fmaf(w0, cc[l * l + 1], as);
+            }
+        }
+        gv[2 * mm] = ac + bc;
+        gv[2 * mm + 1] = as + bs;
+    }
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float x0 = gv[2 * c], x1 = gv[2 * c + 1];
+        const uint32_t t0 = pack_bf16x2(x0, x1);
+        const float r0 = x0 - bf16lo_to_f32(t0), r1 = x1 - bf16hi_to_f32(t0);
+        const uint32_t t1 = pack_bf16x2(r0, r1);
+        w0[c] = t0;
+        w1[c] = t1;
+        if (A_TERMS == 3) w2[c] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
+    }
+    const size_t a_term_bytes = (size_t)128 * Kpad * 2;
+    const int r = (int)(row & 127);
+    uint8_t *dst = Aop + (size_t)(row >> 7) * A_TERMS * a_term_bytes + (size_t)(r >> 3) * (Kpad * 16) + (r & 7) * 16 +
+                   gi * 128;
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    *reinterpret_cast<uint4 *>(dst + a_term_bytes) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    if (A_TERMS == 3) *reinterpret_cast<uint4 *>(dst + 2 * a_term_bytes) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+}
+
+// ----------------------------------------------------------------------------
+// (d) reconstruction, part 2: phi synthesis on tcgen05
+//   Phi[row][k] = G[row][0] + sum_{p>=1} G[row][p] Iph[p][k] / dphi_k
+// Warp 0 bulk-copies each tile's A operand (+ its m = 0 column) into a 2-deep
+// ring and the pre-split table (resident when it fits, else a ring); warp 1
+// issues the MMAs into double-buffered [128 x NC] fp32 accumulators; warps
+// 2..17 (four per tensor-memory lane quarter) drain the accumulators, add the
+// m = 0 term, pack float64 with integer ops into swizzled staging boxes and
+// write Phi with TMA stores.
 // ----------------------------------------------------------------------------
 namespace synth {
 constexpr int STG_BYTES = 32 * 16 * 8;  // TMA store box [32 rows][16 float64], 128B swizzle
-constexpr int JB = 32;                  // polar cells per tile in polar-block mode
+constexpr int EPI_WARPS = 16;
+constexpr int THREADS = (2 + EPI_WARPS) * 32;
 }
 
 struct SynthParams {
+    const uint8_t *Aop;    // [tiles][A_TERMS][128 x Kpad] bf16, canonical layout
+    const float *G0;       // [R]
     const uint8_t *tabT;   // [n_nc][Kpad/16][3][NC x 16] bf16, canonical layout
-    const float *C32;      // [n_r][KL]
-    const float *Itc;      // [T][n_t]  Ith / dmu
     int *err;
     long long R;
-    int n_r, n_t, L, KL, T, P, Kpad, NC, n_nc, ns_b;
-    int jblock;            // 1: tiles of (128/JB shells x JB polar cells), table slice in shared memory
-    int n_ib;              // shell blocks per polar block (polar-block mode)
-    int n_items;           // tiles in total
+    int Kpad, NC, n_nc, n_tiles, ns_a, ns_b, stg_bufs;
+    int b_resident;        // 1: every table chunk stays in shared memory for the whole launch
+    uint32_t a_bytes;      // one tile's A operand (all terms)
     uint32_t bchunk;       // bytes of one B chunk (3 terms)
 };
 
-// Tile -> (first shell, first polar cell) in polar-block mode; rows r of the
-// tile are (shell i0 + r / JB, polar cell j0 + r % JB).
-__device__ __forceinline__ void synth_item(const SynthParams &prm, int item, int &i0, int &j0)
-{
-    const int jb = item / prm.n_ib, ib = item % prm.n_ib;
-    i0 = ib * (kBM / synth::JB);
-    j0 = jb * synth::JB;
-}
-
 template <int A_TERMS, int NPROD>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(synth::THREADS, 1)
     k_synth_tc(const __grid_constant__ CUtensorMap tmPhi, const SynthParams prm)
 {
     using namespace synth;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int NS_B = prm.ns_b;
+    const int NS_A = prm.ns_a, NS_B = prm.ns_b, NSTG = prm.stg_bufs;
     const int Kpad = prm.Kpad, NC = prm.NC;
-    const int a_term_bytes = kBM * Kpad * 2;
-    const int SB = kBM / JB;
-    uint8_t *stg = smem;                                          // [8 warps][2][4096]
-    uint8_t *sA = stg + (size_t)kConvWarps * 2 * STG_BYTES;       // [A_TERMS][128 x Kpad]
-    uint8_t *sB = sA + (size_t)A_TERMS * a_term_bytes;            // [NS_B][bchunk]
-    float *sItc = reinterpret_cast<float *>(sB + (size_t)NS_B * prm.bchunk);  // [T][JB] (polar-block mode)
-    float *sC = sItc + (prm.jblock ? (size_t)prm.T * JB : 0);     // [SB][KL] (polar-block mode)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(
-        (reinterpret_cast<uintptr_t>(sC + (prm.jblock ? (size_t)SB * prm.KL : 0)) + 15) & ~uintptr_t(15));
-    uint64_t *a_full = bars, *a_empty = bars + 1;
-    uint64_t *b_full = bars + 2, *b_empty = b_full + NS_B;
+    const int nkk = Kpad / 16;
+    const int n_chunks = prm.n_nc * nkk;
+    const int b_slots = prm.b_resident ? n_chunks : NS_B;
+    const uint32_t a_stage = prm.a_bytes + 512;  // A operand terms + the tile's 128 m = 0 values
+    uint8_t *stg = smem;                                           // [16 warps][NSTG][4096]
+    uint8_t *sA = stg + (size_t)EPI_WARPS * NSTG * STG_BYTES;      // [NS_A][a_stage]
+    uint8_t *sB = sA + (size_t)NS_A * a_stage;                     // [b_slots][bchunk]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)b_slots * prm.bchunk);
+    uint64_t *a_full = bars, *a_empty = bars + NS_A;
+    uint64_t *b_full = a_empty + NS_A, *b_empty = b_full + NS_B;
     uint64_t *acc_full = b_empty + NS_B, *acc_empty = acc_full + 2, *drain = acc_empty + 2;
-    uint64_t *c_free = drain + 1, *c_ready = drain + 2;  // compute warps: staged rows free / loaded
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 3);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t ncols = tmem_ncols_for(2 * NC);
     const uint32_t acc_stride = ncols / 2;
-    const int nkk = Kpad / 16;
-    // contiguous range of tiles of this CTA (consecutive tiles share a polar block)
-    const int it0 = (int)((long long)prm.n_items * blockIdx.x / gridDim.x);
-    const int it1 = (int)((long long)prm.n_items * (blockIdx.x + 1) / gridDim.x);
 
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(a_full), kConvWarps);
-        mbar_init(smem_u32(a_empty), 1);
+        for (int s = 0; s < NS_A; ++s) {
+            mbar_init(smem_u32(&a_full[s]), 1);
+            mbar_init(smem_u32(&a_empty[s]), 1 + EPI_WARPS);  // MMAs done and m = 0 values read
+        }
         for (int s = 0; s < NS_B; ++s) {
             mbar_init(smem_u32(&b_full[s]), 1);
             mbar_init(smem_u32(&b_empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&acc_full[b]), 1);
-            mbar_init(smem_u32(&acc_empty[b]), kConvWarps);
+            mbar_init(smem_u32(&acc_empty[b]), EPI_WARPS);
         }
         mbar_init(smem_u32(drain), 1);
-        mbar_init(smem_u32(c_free), kConvWarps);
-        mbar_init(smem_u32(c_ready), kConvWarps);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -427,33 +717,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
+    // set-up (and, in the producer, the table copy) overlaps the previous kernel's tail; the
+    // A tiles and the potential are touched only after it has completed
+    pdl_trigger();
+    if (warp != 0) pdl_wait();
 
     if (warp == 0) {
-        // ---------------- producer: table chunks (nc, kk) for every tile
+        // ---------------- producer: A tiles (+ m = 0 column) and table chunks
         if (lane == 0) {
-            Ring rb;
-            int issued = 0;
             bool ok = true;
-            for (int it = it0; it < it1 && ok; ++it)
-                for (int nc = 0; nc < prm.n_nc && ok; ++nc)
-                    for (int kk = 0; kk < nkk; ++kk, rb.next(NS_B)) {
+            if (prm.b_resident && blockIdx.x < prm.n_tiles) {
+                // the whole table once; b_full[0] completes when every chunk has landed
+                mbar_arrive_expect_tx(smem_u32(&b_full[0]), (uint32_t)n_chunks * prm.bchunk);
+                for (int c = 0; c < n_chunks; ++c)
+                    bulk_load(smem_u32(sB + (size_t)c * prm.bchunk), prm.tabT + (size_t)c * prm.bchunk, prm.bchunk,
+                              smem_u32(&b_full[0]));
+            }
+            pdl_wait();
+            Ring ra, rb;
+            for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ra.next(NS_A)) {
+                ok = mbar_wait(smem_u32(&a_empty[ra.idx]), ra.phase ^ 1, abort_flag, prm.err);
+                if (!ok) break;
+                const uint32_t fb = smem_u32(&a_full[ra.idx]);
+                uint8_t *dst = sA + (size_t)ra.idx * a_stage;
+                mbar_arrive_expect_tx(fb, a_stage);
+                bulk_load(smem_u32(dst), prm.Aop + (size_t)tile * prm.a_bytes, prm.a_bytes, fb);
+                bulk_load(smem_u32(dst + prm.a_bytes), prm.G0 + (size_t)tile * 128, 512, fb);
+                if (!prm.b_resident) {
+                    for (int c = 0; c < n_chunks && ok; ++c, rb.next(NS_B)) {
                         ok = mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err);
                         if (!ok) break;
                         mbar_arrive_expect_tx(smem_u32(&b_full[rb.idx]), prm.bchunk);
-                        bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bchunk),
-                                  prm.tabT + ((size_t)nc * nkk + kk) * prm.bchunk, prm.bchunk,
-                                  smem_u32(&b_full[rb.idx]));
-                        ++issued;
+                        bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bchunk), prm.tabT + (size_t)c * prm.bchunk,
+                                  prm.bchunk, smem_u32(&b_full[rb.idx]));
                     }
-            if (*abort_flag && issued > 0) {
-                Ring back = rb;
-                for (int n = 0; n < NS_B && n < issued; ++n) {
-                    back.idx = (back.idx == 0) ? NS_B - 1 : back.idx - 1;
-                    if (back.idx == NS_B - 1) back.phase ^= 1u;
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait(smem_u32(&b_full[back.idx]), back.phase) &&
-                           clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
-                    }
+                }
+            }
+            if (*abort_flag) {
+                // let copies already issued into this CTA's shared memory land (bounded)
+                const long long t0 = clock64();
+                while (clock64() - t0 < 100000) {
                 }
             }
         }
@@ -462,40 +765,49 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(kBM, NC);
             const uint32_t sbo_a = (uint32_t)Kpad * 16;
-            Ring rb;
+            const uint32_t a_term_bytes = (uint32_t)kBM * Kpad * 2;
+            Ring ra, rb;
             uint32_t u = 0;
-            int lt = 0;
             bool ok = true;
-            for (int it = it0; it < it1 && ok; ++it, ++lt) {
-                ok = mbar_wait(smem_u32(a_full), lt & 1, abort_flag, prm.err);
+            if (prm.b_resident && blockIdx.x < prm.n_tiles) ok = mbar_wait(smem_u32(&b_full[0]), 0, abort_flag, prm.err);
+            for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ra.next(NS_A)) {
+                ok = mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err);
                 if (!ok) break;
                 tc_fence_after();
+                const uint32_t a_base0 = smem_u32(sA + (size_t)ra.idx * a_stage);
                 for (int nc = 0; nc < prm.n_nc && ok; ++nc, ++u) {
                     const int buf = u & 1;
                     ok = mbar_wait(smem_u32(&acc_empty[buf]), ((u >> 1) & 1) ^ 1, abort_flag, prm.err);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)buf * acc_stride;
-                    for (int kk = 0; kk < nkk; ++kk, rb.next(NS_B)) {
-                        ok = mbar_wait(smem_u32(&b_full[rb.idx]), rb.phase, abort_flag, prm.err);
-                        if (!ok) break;
-                        tc_fence_after();
-                        const uint32_t a_base = smem_u32(sA) + (uint32_t)(kk * 256);
-                        const uint32_t b_base = smem_u32(sB + (size_t)rb.idx * prm.bchunk);
+                    for (int kk = 0; kk < nkk; ++kk) {
+                        uint32_t b_base;
+                        if (prm.b_resident) {
+                            b_base = smem_u32(sB + (size_t)(nc * nkk + kk) * prm.bchunk);
+                        } else {
+                            ok = mbar_wait(smem_u32(&b_full[rb.idx]), rb.phase, abort_flag, prm.err);
+                            if (!ok) break;
+                            tc_fence_after();
+                            b_base = smem_u32(sB + (size_t)rb.idx * prm.bchunk);
+                        }
+                        const uint32_t a_base = a_base0 + (uint32_t)(kk * 256);
 #pragma unroll
                         for (int pi = 0; pi < NPROD; ++pi) {
-                            const uint64_t ad =
-                                sdesc_noswizzle(a_base + (uint32_t)(c_prod_a[pi] * a_term_bytes), 128, sbo_a);
+                            const uint64_t ad = sdesc_noswizzle(a_base + c_prod_a[pi] * a_term_bytes, 128, sbo_a);
                             const uint64_t bd = sdesc_noswizzle(b_base + (uint32_t)(c_prod_b[pi] * NC * 32), 128, 256);
                             umma_bf16(d_tmem, ad, bd, idesc, (kk | pi) != 0);
                         }
-                        umma_commit(smem_u32(&b_empty[rb.idx]));
+                        if (!prm.b_resident) {
+                            umma_commit(smem_u32(&b_empty[rb.idx]));
+                            rb.next(NS_B);
+                        }
                     }
                     if (!ok) break;
                     umma_commit(smem_u32(&acc_full[buf]));
                 }
                 if (!ok) break;
-                umma_commit(smem_u32(a_empty));
+                umma_commit(smem_u32(&a_empty[ra.idx]));
             }
             umma_commit(smem_u32(drain));
             const long long t0 = clock64();
@@ -503,172 +815,55 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // ---------------- theta synthesis (A operand) + epilogue (Phi)
-        const int cw = warp - 2, qd = warp & 3, half = cw >> 2;
+        // ---------------- epilogue: accumulators -> Phi
+        const int cw = warp - 2, qd = warp & 3, quarter = cw >> 2;
         const int row = qd * 32 + lane;
-        const int ctid = threadIdx.x - 64;  // 0..255 among the compute warps
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
-        const int n_t = prm.n_t, L = prm.L, KL = prm.KL;
+        Ring ra;
         uint32_t u = 0, cs = 0;
-        int lt = 0, cur_j0 = -1;
         bool ok = true;
-        for (int it = it0; it < it1 && ok; ++it, ++lt) {
-            ok = warp_all(mbar_wait(smem_u32(a_empty), (lt & 1) ^ 1, abort_flag, prm.err));
+        for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ra.next(NS_A)) {
+            ok = warp_all(mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err));
             if (!ok) break;
-            // rows of this tile: (shell i, polar cell j) and the first memory row of this warp's box
-            int i, j;
-            long long box_row;
-            bool valid;
-            const float *crow;    // coefficients C[i][*] of this row's shell
-            const float *itab;    // table Itc[t][j], stride tstride in t
-            int tstride;
-            if (prm.jblock) {
-                int i0, j0;
-                synth_item(prm, it, i0, j0);
-                i = i0 + row / JB;
-                j = j0 + row % JB;
-                valid = i < prm.n_r;
-                box_row = (long long)(i0 + (qd * 32) / JB) * n_t + j0 + (qd * 32) % JB;
-                // every compute warp is done with the previous tile's staged rows
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(c_free));
-                ok = warp_all(mbar_wait(smem_u32(c_free), lt & 1, abort_flag, prm.err));
-                if (!ok) break;
-                if (j0 != cur_j0) {
-                    for (int e = ctid; e < prm.T * JB; e += 256)
-                        sItc[e] = __ldg(prm.Itc + (size_t)(e / JB) * n_t + j0 + e % JB);
-                    cur_j0 = j0;
-                }
-                for (int e = ctid; e < SB * KL; e += 256) {
-                    const int si = i0 + e / KL;
-                    sC[e] = (si < prm.n_r) ? __ldg(prm.C32 + (size_t)si * KL + e % KL) : 0.0f;
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(c_ready));
-                ok = warp_all(mbar_wait(smem_u32(c_ready), lt & 1, abort_flag, prm.err));
-                if (!ok) break;
-                crow = sC + (row / JB) * KL;
-                itab = sItc + row % JB;
-                tstride = JB;
-            } else {
-                const long long grow = (long long)it * kBM + row;
-                valid = grow < prm.R;
-                i = valid ? (int)(grow / n_t) : 0;
-                j = valid ? (int)(grow % n_t) : 0;
-                box_row = (long long)it * kBM + qd * 32;
-                crow = prm.C32 + (size_t)i * KL;
-                itab = prm.Itc + j;
-                tstride = n_t;
-            }
-            (void)i;
-            (void)j;
-            float g0 = 0.0f, g1 = 0.0f;
-            if (valid) {
-                int l = 0;
-                for (; l + 1 <= L; l += 2) {
-                    g0 = fmaf(itab[(size_t)tri(l, 0) * tstride], crow[l * l], g0);
-                    g1 = fmaf(itab[(size_t)tri(l + 1, 0) * tstride], crow[(l + 1) * (l + 1)], g1);
-                }
-                if (l <= L) g0 = fmaf(itab[(size_t)tri(l, 0) * tstride], crow[l * l], g0);
-                g0 += g1;
-            }
-            // A operand: G[row][p], p = 1..2L, stored at K index p-1, in A_TERMS bf16 terms.
-            // Group gi holds p = 8 gi + 1 .. 8 gi + 8, the cos/sin pairs of m = 4 gi + 1 .. 4 gi + 4;
-            // each table value serves both members of a pair.
-            for (int gi = half; gi < Kpad / 8; gi += 2) {
-                float gv[8];
-#pragma unroll
-                for (int mm = 0; mm < 4; ++mm) {
-                    const int m = 4 * gi + mm + 1;
-                    float ac = 0.0f, as = 0.0f, bc = 0.0f, bs = 0.0f;
-                    if (valid && m <= L) {
-                        const float *cc = crow + 2 * m - 1;  // C[i][l^2 + 2m - 1], C[i][l^2 + 2m]
-                        int l = m;
-                        for (; l + 1 <= L; l += 2) {
-                            const float w0 = itab[(size_t)tri(l, m) * tstride];
-                            const float w1 = itab[(size_t)tri(l + 1, m) * tstride];
-                            ac = fmaf(w0, cc[l * l], ac);
-                            as = fmaf(w0, cc[l * l + 1], as);
-                            bc = fmaf(w1, cc[(l + 1) * (l + 1)], bc);
-                            bs = fmaf(w1, cc[(l + 1) * (l + 1) + 1], bs);
-                        }
-                        if (l <= L) {
-                            const float w0 = itab[(size_t)tri(l, m) * tstride];
-                            ac = fmaf(w0, cc[l * l], ac);
-                            as = fmaf(w0, cc[l * l + 1], as);
-                        }
-                    }
-                    gv[2 * mm] = ac + bc;
-                    gv[2 * mm + 1] = as + bs;
-                }
-                uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const float x0 = gv[2 * cc], x1 = gv[2 * cc + 1];
-                    const uint32_t t0 = pack_bf16x2(x0, x1);
-                    const float r0 = x0 - bf16lo_to_f32(t0), r1 = x1 - bf16hi_to_f32(t0);
-                    const uint32_t t1 = pack_bf16x2(r0, r1);
-                    w0[cc] = t0;
-                    w1[cc] = t1;
-                    if (A_TERMS == 3) w2[cc] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
-                }
-                uint8_t *adst = sA + (size_t)(row >> 3) * (Kpad * 16) + gi * 128 + (row & 7) * 16;
-                *reinterpret_cast<uint4 *>(adst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                *reinterpret_cast<uint4 *>(adst + a_term_bytes) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                if (A_TERMS == 3)
-                    *reinterpret_cast<uint4 *>(adst + 2 * a_term_bytes) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-            }
-            fence_proxy_async_smem();
+            const float g0 = reinterpret_cast<const float *>(sA + (size_t)ra.idx * a_stage + prm.a_bytes)[row];
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(a_full));
-
-            // a box of 32 rows is written only when its first row is a real row
-            const bool box_valid = prm.jblock ? (__shfl_sync(kFull, valid ? 1 : 0, 0) != 0) : (box_row < prm.R);
-            int nc_cur = 0;
-            // converts 16 accumulator columns of this row (+ the m = 0 term) to float64 in a
-            // swizzled staging box and hands the box to a TMA store
-            auto store_chunk = [&](const uint32_t(&v)[16], int ch) {
-                uint8_t *st = stg + (size_t)(cw * 2 + (cs & 1)) * STG_BYTES;
-                ++cs;
-                if (lane == 0) bulk_wait_read_le1();
-                __syncwarp();
-                uint8_t *srow = st + lane * 128;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    uint32_t lo0, hi0, lo1, hi1;
-                    f32_to_f64w_finite(__uint_as_float(v[2 * e]) + g0, lo0, hi0);
-                    f32_to_f64w_finite(__uint_as_float(v[2 * e + 1]) + g0, lo1, hi1);
-                    *reinterpret_cast<uint4 *>(srow + ((e ^ (lane & 7)) << 4)) = make_uint4(lo0, hi0, lo1, hi1);
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0 && box_valid) {
-                    tma_store_2d(&tmPhi, smem_u32(st), nc_cur * NC + ch * 16, (int)box_row);
-                    bulk_commit();
-                }
-            };
+            if (lane == 0) mbar_arrive(smem_u32(&a_empty[ra.idx]));
+            const long long box_row = (long long)tile * kBM + qd * 32;
+            const bool box_valid = box_row < prm.R;
             for (int nc = 0; nc < prm.n_nc && ok; ++nc, ++u) {
-                nc_cur = nc;
                 const int buf = u & 1;
                 ok = warp_all(mbar_wait(smem_u32(&acc_full[buf]), (u >> 1) & 1, abort_flag, prm.err));
                 if (!ok) break;
                 tc_fence_after();
-                // 16-column chunks ch = half, half + 2, ...; the tensor-memory load of the
-                // next chunk is in flight while the current one is converted and stored
-                const int nch = NC / 16;
                 const uint32_t tcol = tmem_base + lane_base + (uint32_t)buf * acc_stride;
-                uint32_t va[16], vb[16];
-                if (half < nch) tmem_ld16(tcol + (uint32_t)(half * 16), va);
-                tmem_ld_wait();
-                for (int ch = half; ch < nch; ch += 4) {
-                    const bool nb = ch + 2 < nch, na = ch + 4 < nch;
-                    if (nb) tmem_ld16(tcol + (uint32_t)((ch + 2) * 16), vb);
-                    store_chunk(va, ch);
-                    if (nb) {
-                        tmem_ld_wait();
-                        if (na) tmem_ld16(tcol + (uint32_t)((ch + 4) * 16), va);
-                        store_chunk(vb, ch + 2);
-                        if (na) tmem_ld_wait();
+                const int nmine = (NC / 16 - quarter + 3) / 4;  // chunks quarter, quarter + 4, ...
+                for (int it = 0; it < nmine; ++it) {
+                    const int ch = quarter + 4 * rotated_chunk(it, tile, nmine);
+                    uint32_t v[16];
+                    tmem_ld16(tcol + (uint32_t)(ch * 16), v);
+                    tmem_ld_wait();
+                    uint8_t *st = stg + (size_t)(cw * NSTG + (cs % NSTG)) * STG_BYTES;
+                    ++cs;
+                    if (lane == 0) {
+                        if (NSTG > 1)
+                            bulk_wait_read_le1();
+                        else
+                            bulk_wait_read_all();
+                    }
+                    __syncwarp();
+                    uint8_t *srow = st + lane * 128;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        uint32_t lo0, hi0, lo1, hi1;
+                        f32_to_f64w_finite(__uint_as_float(v[2 * e]) + g0, lo0, hi0);
+                        f32_to_f64w_finite(__uint_as_float(v[2 * e + 1]) + g0, lo1, hi1);
+                        *reinterpret_cast<uint4 *>(srow + ((e ^ (lane & 7)) << 4)) = make_uint4(lo0, hi0, lo1, hi1);
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0 && box_valid) {
+                        tma_store_2d(&tmPhi, smem_u32(st), nc * NC + ch * 16, (int)box_row);
+                        bulk_commit();
                     }
                 }
                 tc_fence_before();
@@ -762,16 +957,16 @@ __global__ void k_tab_synth(const double *__restrict__ Iphc, int n_p, int P, int
     *reinterpret_cast<uint16_t *>(base + (size_t)2 * NC * 32 + off) = b2;
 }
 
-// float32 theta tables: IthT[j][t] = Ith[t][j], Itc[t][j] = Ith[t][j] / dmu_j
-__global__ void k_tab_theta32(const double *__restrict__ Ith, const double *__restrict__ dmu, int n_t, int T,
-                              float *__restrict__ IthT, float *__restrict__ Itc)
+// float32 theta tables (rows of ldF cells): Ith32[t][j] = Ith[t][j], Itc[t][j] = Ith[t][j] / dmu_j
+__global__ void k_tab_theta32(const double *__restrict__ Ith, const double *__restrict__ dmu, int n_t, int T, int ldF,
+                              float *__restrict__ Ith32, float *__restrict__ Itc)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)T * n_t) return;
     const int t = (int)(idx / n_t), j = (int)(idx % n_t);
     const double v = Ith[idx];
-    IthT[(size_t)j * T + t] = (float)v;
-    Itc[idx] = (float)(v / dmu[j]);
+    Ith32[(size_t)t * ldF + j] = (float)v;
+    Itc[(size_t)t * ldF + j] = (float)(v / dmu[j]);
 }
 
 template <int A_TERMS, int NPROD>
@@ -783,17 +978,20 @@ cudaError_t set_smem_attrs(int proj_smem, int synth_smem)
     return cudaFuncSetAttribute(k_synth_tc<A_TERMS, NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, synth_smem);
 }
 
+// B terms the products read: x3 uses b0 and b1, x6 also b2
+int proj_b_terms(const SplitPlan &pl) { return pl.n_products == 3 ? 2 : 3; }
+
 int proj_smem_bytes(const SplitPlan &pl, int ns_s, int ns_o)
 {
-    const int bchunk = 3 * pl.Npad * proj::BK * 2;
-    return 1024 + ns_s * proj::S_BYTES + ns_s * bchunk + ns_o * pl.a_terms * proj::A_TERM_BYTES + 512;
+    const int bload = proj_b_terms(pl) * pl.Npad * proj::BK * 2;
+    return 1024 + ns_s * proj::S_BYTES + ns_s * bload + ns_o * pl.a_terms * proj::A_TERM_BYTES + 512;
 }
 
-int synth_smem_bytes(const SplitPlan &pl, int ns_b, int jblock, int T, int KL)
+int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs)
 {
     const int bchunk = 3 * pl.NC * 32;
-    const int tabs = jblock ? (T * synth::JB + (kBM / synth::JB) * KL) * 4 + 16 : 0;
-    return 1024 + kConvWarps * 2 * synth::STG_BYTES + pl.a_terms * kBM * pl.Kpad * 2 + ns_b * bchunk + tabs + 256;
+    const int a_stage = pl.a_terms * kBM * pl.Kpad * 2 + 512;
+    return 1024 + synth::EPI_WARPS * stg_bufs * synth::STG_BYTES + ns_a * a_stage + b_slots * bchunk + 512;
 }
 
 constexpr int kSmemLimit = 232448;  // 227 KB opt-in per block on sm_100-class parts
@@ -807,21 +1005,28 @@ int split_smem_limits(mp_mesh *m)
     int ns_s = 4;
     while (ns_s > 2 && proj_smem_bytes(pl, ns_s, 2) > kSmemLimit) --ns_s;
     if (proj_smem_bytes(pl, ns_s, 2) > kSmemLimit) return 1;
-    // polar-block tiles when the polar cells split into blocks of 32 and the table slice fits
-    int jblock = (m->n_t % synth::JB == 0) ? 1 : 0;
-    int ns_b = 3;
-    while (ns_b > 2 && synth_smem_bytes(pl, ns_b, jblock, m->T, m->KL) > kSmemLimit) --ns_b;
-    if (jblock && synth_smem_bytes(pl, ns_b, jblock, m->T, m->KL) > kSmemLimit) {
-        jblock = 0;
-        ns_b = 3;
-        while (ns_b > 2 && synth_smem_bytes(pl, ns_b, 0, m->T, m->KL) > kSmemLimit) --ns_b;
+    // synthesis: prefer the whole table resident, two A stages and double-buffered staging
+    const int n_chunks = pl.n_nc * (pl.Kpad / 16);
+    struct Cfg {
+        int ns_a, resident, ns_b, stg;
+    };
+    const Cfg cfgs[] = {{2, 1, 0, 2}, {2, 0, 3, 2}, {2, 0, 2, 2}, {1, 0, 2, 2}, {2, 0, 2, 1}, {1, 0, 2, 1}};
+    bool found = false;
+    for (const Cfg &c : cfgs) {
+        const int b_slots = c.resident ? n_chunks : c.ns_b;
+        if (synth_smem_bytes(pl, c.ns_a, b_slots, c.stg) <= kSmemLimit) {
+            pl.ns_a = c.ns_a;
+            pl.b_resident = c.resident;
+            pl.ns_b = c.resident ? 1 : c.ns_b;
+            pl.stg_bufs = c.stg;
+            pl.synth_smem = synth_smem_bytes(pl, c.ns_a, b_slots, c.stg);
+            found = true;
+            break;
+        }
     }
-    if (synth_smem_bytes(pl, ns_b, jblock, m->T, m->KL) > kSmemLimit) return 2;
-    pl.jblock = jblock;
+    if (!found) return 2;
     pl.proj_smem = proj_smem_bytes(pl, ns_s, 2);
-    pl.synth_smem = synth_smem_bytes(pl, ns_b, jblock, m->T, m->KL);
     pl.ns_s = ns_s;
-    pl.ns_b = ns_b;
     return 0;
 }
 
@@ -840,8 +1045,8 @@ cudaError_t launch_split_tables(mp_mesh *m)
     }
     {
         const long long n = (long long)m->T * m->n_t;
-        k_tab_theta32<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(m->d_Ith, m->d_dmu, m->n_t, m->T,
-                                                                          m->d_IthT32, m->d_Itc32);
+        k_tab_theta32<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(m->d_Ith, m->d_dmu, m->n_t, m->T, pl.ldF,
+                                                                          m->d_Ith32, m->d_Itc32);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -852,11 +1057,14 @@ cudaError_t launch_split_tables(mp_mesh *m)
 
 cudaError_t launch_split_project(mp_mesh *m, const double *rho)
 {
-    (void)rho;
     const SplitPlan &pl = m->plan;
     ProjParams prm;
     prm.tabB = m->d_tabB;
     prm.colsum = m->d_colsum;
+    prm.rho = rho;
+    prm.n_t = m->n_t;
+    prm.P = m->P;
+    prm.ldF = pl.ldF;
     prm.F = m->d_F32;
     prm.err = m->d_err;
     prm.R = m->R;
@@ -867,13 +1075,14 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho)
     prm.ns_s = pl.ns_s;
     prm.ns_o = 2;
     prm.bchunk = (uint32_t)(3 * pl.Npad * proj::BK * 2);
+    prm.bload = (uint32_t)(proj_b_terms(pl) * pl.Npad * proj::BK * 2);
     const int grid = std::min(prm.n_tiles, pl.proj_ctas);
     cudaEvent_t ev;
     prof_begin(m, "split_phi_project_tc", &ev);
     if (pl.a_terms == 2)
-        k_proj_tc<2, 3><<<grid, kThreads, pl.proj_smem, m->stream>>>(m->tm_rho, prm);
+        launch_pdl(k_proj_tc<2, 3>, dim3(grid), dim3(kProjThreads), pl.proj_smem, m->stream, m->tm_rho, prm);
     else
-        k_proj_tc<3, 6><<<grid, kThreads, pl.proj_smem, m->stream>>>(m->tm_rho, prm);
+        launch_pdl(k_proj_tc<3, 6>, dim3(grid), dim3(kProjThreads), pl.proj_smem, m->stream, m->tm_rho, prm);
     prof_end(m, "split_phi_project_tc", ev);
     return cudaGetLastError();
 }
@@ -882,39 +1091,68 @@ cudaError_t launch_split_synth(mp_mesh *m, double *phi)
 {
     (void)phi;
     const SplitPlan &pl = m->plan;
+    const int n_tiles = (int)((m->R + kBM - 1) / kBM);
+    cudaEvent_t ev;
+    prof_begin(m, "split_theta_synth", &ev);
+    const int ngrp = pl.Kpad / 8 + 1;  // K groups plus the m = 0 column
+    const uint32_t tab_bytes = (uint32_t)((size_t)m->T * pl.ldF * 4);
+    const int U = 1 + (m->L + 1) / 2, NJ = ((m->n_t + 3) / 4 + 31) / 32;
+    const int pipe_threads = std::min(1024, kGsS * NJ * U * 32);
+    const size_t pipe_smem = (size_t)tab_bytes + (size_t)kGsS * pl.Kpad * pl.ldF * 4 +
+                             (((size_t)kGsS * m->KL + 1) & ~(size_t)1) * 4 + 16;
+    if (pipe_smem <= 200 * 1024 && kGsS * m->KL <= kGsPre * pipe_threads) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_gsynth_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(k_gsynth_pipe<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr_set = true;
+        }
+        const int grid = std::min((m->n_r + kGsS - 1) / kGsS, m->num_sms);
+        if (pl.a_terms == 2)
+            launch_pdl(k_gsynth_pipe<2>, dim3(grid), dim3(pipe_threads), pipe_smem, m->stream, m->d_C32, m->d_Itc32,
+                       m->d_Aop, m->d_G0, m->d_err, m->n_r, m->n_t, m->L, m->KL, pl.Kpad, pl.ldF, tab_bytes);
+        else
+            launch_pdl(k_gsynth_pipe<3>, dim3(grid), dim3(pipe_threads), pipe_smem, m->stream, m->d_C32, m->d_Itc32,
+                       m->d_Aop, m->d_G0, m->d_err, m->n_r, m->n_t, m->L, m->KL, pl.Kpad, pl.ldF, tab_bytes);
+    } else {
+        const int jpb = std::max(1, std::min(m->n_t, 256 / ngrp));
+        const dim3 block(ngrp, jpb);
+        const dim3 grid(m->n_r, (m->n_t + jpb - 1) / jpb);
+        const size_t smem = (size_t)m->KL * sizeof(float);
+        if (smem > 48 * 1024) {
+            cudaFuncSetAttribute(k_gsynth<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_gsynth<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        }
+        if (pl.a_terms == 2)
+            k_gsynth<2><<<grid, block, smem, m->stream>>>(m->d_C32, m->d_Itc32, m->d_Aop, m->d_G0, m->n_t, m->L,
+                                                          m->KL, pl.Kpad, pl.ldF);
+        else
+            k_gsynth<3><<<grid, block, smem, m->stream>>>(m->d_C32, m->d_Itc32, m->d_Aop, m->d_G0, m->n_t, m->L,
+                                                          m->KL, pl.Kpad, pl.ldF);
+    }
+    prof_end(m, "split_theta_synth", ev);
     SynthParams prm;
+    prm.Aop = m->d_Aop;
+    prm.G0 = m->d_G0;
     prm.tabT = m->d_tabT;
-    prm.C32 = m->d_C32;
-    prm.Itc = m->d_Itc32;
     prm.err = m->d_err;
     prm.R = m->R;
-    prm.n_r = m->n_r;
-    prm.n_t = m->n_t;
-    prm.L = m->L;
-    prm.KL = m->KL;
-    prm.T = m->T;
-    prm.P = m->P;
     prm.Kpad = pl.Kpad;
     prm.NC = pl.NC;
     prm.n_nc = pl.n_nc;
+    prm.n_tiles = n_tiles;
+    prm.ns_a = pl.ns_a;
     prm.ns_b = pl.ns_b;
-    prm.jblock = pl.jblock;
-    if (pl.jblock) {
-        const int SB = kBM / synth::JB;
-        prm.n_ib = (m->n_r + SB - 1) / SB;
-        prm.n_items = prm.n_ib * (m->n_t / synth::JB);
-    } else {
-        prm.n_ib = 0;
-        prm.n_items = (int)((m->R + kBM - 1) / kBM);
-    }
+    prm.stg_bufs = pl.stg_bufs;
+    prm.b_resident = pl.b_resident;
+    prm.a_bytes = (uint32_t)(pl.a_terms * kBM * pl.Kpad * 2);
     prm.bchunk = (uint32_t)(3 * pl.NC * 32);
-    const int grid = std::min(prm.n_items, pl.synth_ctas);
-    cudaEvent_t ev;
+    const int grid = std::min(n_tiles, pl.synth_ctas);
     prof_begin(m, "split_synth_tc", &ev);
     if (pl.a_terms == 2)
-        k_synth_tc<2, 3><<<grid, kThreads, pl.synth_smem, m->stream>>>(m->tm_phi, prm);
+        launch_pdl(k_synth_tc<2, 3>, dim3(grid), dim3(synth::THREADS), pl.synth_smem, m->stream, m->tm_phi, prm);
     else
-        k_synth_tc<3, 6><<<grid, kThreads, pl.synth_smem, m->stream>>>(m->tm_phi, prm);
+        launch_pdl(k_synth_tc<3, 6>, dim3(grid), dim3(synth::THREADS), pl.synth_smem, m->stream, m->tm_phi, prm);
     prof_end(m, "split_synth_tc", ev);
     return cudaGetLastError();
 }

@@ -10,7 +10,7 @@
 //                    the cancellation-free product form 2 trig(m mid) sin(m h)/m;
 //   WR[l][i], WI[l][i] = shell integrals of r^2 (r/r_ref)^l and
 //                    r^2 r_ref^l / r^(l+1), V[i] = Delta(r^3/3), in
-//                    x0^p expm1(p log1p(dx/x0)) form; RR = WR/V, RI = WI/V.
+//                    x0^p expm1(p log1p(dx/x0)) form; R^R = WR/V, R^I = WI/V.
 // The solid-angle mean of the kernel over cell (j, k) is
 // (Ith/dmu_j)(Iph/dphi_k), dmu_j = cos th_j - cos th_j+1 = 2 sin(mid) sin(half).
 #include <cmath>
@@ -147,10 +147,12 @@ __device__ double pow_diff(double x0, double x1, double p)
 }
 
 // One thread per (l, i): radial shell integrals.  At r_0 = 0 and l >= 2 the
-// irregular integral diverges; WI and RI are stored as 0 there and the
-// recurrences treat that shell's own term separately.
+// irregular integral diverges; WI and GI are stored as 0 there and the
+// recurrences treat that shell's own term separately.  GR and GI are the
+// cell-average radial factors R^R = WR/V and R^I = WI/V of Eq. (Solution)
+// times the m = 0 coefficient prefactor -1/(2 (2l+1)).
 __global__ void k_radial_tables(int L, int n_r, const double *__restrict__ r, double r_ref, double *__restrict__ WR,
-                                double *__restrict__ WI, double *__restrict__ RR, double *__restrict__ RI,
+                                double *__restrict__ WI, double *__restrict__ GR, double *__restrict__ GI,
                                 double *__restrict__ V)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,8 +180,9 @@ __global__ void k_radial_tables(int L, int n_r, const double *__restrict__ r, do
     }
     WR[(size_t)l * n_r + i] = wr;
     WI[(size_t)l * n_r + i] = wi;
-    RR[(size_t)l * n_r + i] = wr / vol;
-    RI[(size_t)l * n_r + i] = wi / vol;
+    const double hp = -0.5 / (2.0 * l + 1.0);
+    GR[(size_t)l * n_r + i] = hp * (wr / vol);
+    GI[(size_t)l * n_r + i] = hp * (wi / vol);
     if (l == 0) V[i] = vol;
 }
 
@@ -210,7 +213,7 @@ cudaError_t launch_tables(mp_mesh *m)
     {
         const int n = (L + 1) * m->n_r;
         k_radial_tables<<<(n + 255) / 256, 256, 0, m->stream>>>(L, m->n_r, m->d_r, m->r_ref, m->d_WR, m->d_WI,
-                                                                m->d_RR, m->d_RI, m->d_V);
+                                                                m->d_GR, m->d_GI, m->d_V);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -75,6 +75,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// Blocks until the grids this one depends on (the previous kernel on the
+// stream, when launched with programmatic stream serialization) have completed
+// and their memory is visible; returns at once otherwise.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Lets the next kernel on the stream start its blocks once every block of this
+// grid has issued the trigger or exited (so a block of this grid never waits
+// for resources held by waiting dependents); they still wait in pdl_wait for
+// this grid to complete.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // ---------------------------------------------------------------- TMA / bulk copies
 __device__ __forceinline__ void tma_prefetch_desc(const void *map)
 {
@@ -107,6 +119,8 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
 __device__ __forceinline__ void bulk_wait_read_le1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -240,6 +254,21 @@ __device__ __forceinline__ float f64w_to_f32_fast(uint32_t lo, uint32_t hi, uint
     return __uint_as_float(r);
 }
 
+// float64 -> float32 with integer ops (round to nearest, ties away from zero):
+// magnitudes below float32's normal range give signed zero, above it signed
+// infinity (so do inf and nan).
+__device__ __forceinline__ float f64_to_f32_alu(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const uint32_t hi = static_cast<uint32_t>(b >> 32);
+    const uint32_t ef = hi & 0x7FF00000u, sign = hi & 0x80000000u;
+    const uint32_t t = static_cast<uint32_t>((b + (1ull << 28)) >> 29);
+    uint32_t r = ((t & 0x7FFFFFFFu) | sign) ^ 0x40000000u;
+    r = (ef < (897u << 20)) ? sign : r;
+    r = (ef > (1150u << 20)) ? (sign | 0x7F800000u) : r;
+    return __uint_as_float(r);
+}
+
 // float32 -> float64 words, exact for normal numbers, integer ops only.
 __device__ __forceinline__ void f32_to_f64w(float x, uint32_t &lo, uint32_t &hi)
 {
@@ -266,6 +295,15 @@ __device__ __forceinline__ void f32_to_f64w_finite(float x, uint32_t &lo, uint32
     const bool normal = mag >= 0x00800000u;
     hi = normal ? h : sign;
     lo = normal ? (b << 29) : 0u;
+}
+
+// float32 -> float64, exact for finite normal inputs (subnormals give zero),
+// integer ops only (the float64 pipe stays free).
+__device__ __forceinline__ double f32_to_f64_alu(float x)
+{
+    uint32_t lo, hi;
+    f32_to_f64w_finite(x, lo, hi);
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // Round-to-nearest bf16 pair packed in one word (x in the low half).

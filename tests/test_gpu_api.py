@@ -45,6 +45,44 @@ def test_solve_without_density_is_not_ready():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_graph_replay_equals_eager_launches_and_follows_rebinding(prec):
+    """mp_solve replays a captured graph; with profiling on it launches the kernels one by
+    one.  Both give identical bits, and binding another density re-captures the graph."""
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = W.presn(n_r=32, n_theta=32, n_phi=64, L=8)
+    w2 = W.presn(n_r=32, n_theta=32, n_phi=64, L=8, seed=7)
+    m = w.mesh
+    rho = torch.from_numpy(w.rho).cuda()
+    rho2 = torch.from_numpy(w2.rho).cuda()
+    phi = torch.empty_like(rho)
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=prec) as mesh:
+        mesh.set_density(rho)
+        mesh.set_phi_output(phi)
+        mesh.solve()
+        mesh.solve()
+        mesh.synchronize()
+        graph_1 = phi.cpu().numpy()
+        mesh.profile(True)
+        mesh.solve()
+        mesh.synchronize()
+        eager_1 = phi.cpu().numpy()
+        mesh.profile(False)
+        mesh.set_density(rho2)
+        mesh.solve()
+        mesh.synchronize()
+        graph_2 = phi.cpu().numpy()
+        mesh.set_density(rho)
+        mesh.solve()
+        mesh.synchronize()
+        graph_1b = phi.cpu().numpy()
+    assert np.array_equal(graph_1, eager_1)
+    assert np.array_equal(graph_1, graph_1b)
+    assert not np.array_equal(graph_1, graph_2)
+    assert phi_rel_err(graph_2, gpu_solve(w2, prec, want_moments=False)["phi"]) == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_host_end_to_end_equals_device_solve(prec):
     import torch
     from paper_2602_02507_gb300 import multipole as mpl
@@ -99,7 +137,8 @@ def test_profile_names_every_kernel():
         for _ in range(3):
             mesh.solve()
         prof = mesh.profile_read()
-    assert set(prof) == {"split_phi_project_tc", "split_theta_contract", "radial_scan", "split_synth_tc"}
+    assert set(prof) == {"split_phi_project_tc", "split_theta_contract", "radial_scan", "split_theta_synth",
+                         "split_synth_tc"}
     assert all(v["launches"] == 3 and v["total_ms"] > 0 for v in prof.values())
 
 
