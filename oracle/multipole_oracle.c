@@ -299,10 +299,13 @@ int orc_radial(int L, int n_r, const double *r, double r_ref, double *WR, double
     return 0;
 }
 
-/* Solid-angle cell widths: dmu_j = cos(theta_j) - cos(theta_{j+1}), dphi_k. */
+/* Solid-angle cell widths: dmu_j = cos(theta_j) - cos(theta_{j+1}) = integral of  */
+/* sin(theta) over the polar cell, and dphi_k.  The difference of cosines is      */
+/* evaluated as 2 sin(mid) sin(half width): near the poles the two cosines agree  */
+/* in their leading digits and their plain difference would lose them.           */
 static void cell_widths(int n_t, const double *th, int n_p, const double *ph, double *dmu, double *dph)
 {
-    for (int j = 0; j < n_t; ++j) dmu[j] = cos(th[j]) - cos(th[j + 1]);
+    for (int j = 0; j < n_t; ++j) dmu[j] = 2.0 * sin(0.5 * (th[j] + th[j + 1])) * sin(0.5 * (th[j + 1] - th[j]));
     for (int k = 0; k < n_p; ++k) dph[k] = ph[k + 1] - ph[k];
 }
 

@@ -51,6 +51,20 @@ def test_spherical_density_has_only_monopole():
     assert np.abs(s["A"][:, 1:]).max() <= 1e-14 * np.abs(s["A"][:, 0]).max()
 
 
+def test_spherical_potential_is_the_same_in_every_polar_cell():
+    """A spherically symmetric density gives each shell one potential value: the cell
+    mean of the monopole kernel is the constant P~_0^0 in every polar cell, including
+    the polar caps of a fine theta mesh, whose solid-angle factor
+    cos(theta_j) - cos(theta_{j+1}) is a difference of nearly equal numbers (formed
+    as that difference, it costs the cap cells of 512 polar cells 1.8e-12; the bound
+    leaves room for the 1e-14 tolerance of the Romberg theta integrals)."""
+    w = _spherical(4, (512, 4), 0.1, 1.0, 2)
+    _, s = _solve(w)
+    phi = s["phi"]
+    spread = np.abs(phi - phi[:, 256:257, :1]).max(axis=(1, 2)) / np.abs(phi).max(axis=(1, 2))
+    assert spread.max() <= 2e-13, spread
+
+
 def test_exterior_potential_of_spherical_mass():
     """Outside all mass: Phi_i = -G M_tot <1/r>_i, <1/r> the shell volume mean."""
     w = _spherical(9, (4, 6), 0.0, 3.0, 4)
