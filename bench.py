@@ -44,9 +44,13 @@ SPLIT_PRECISION = "bf16x3"
 
 # DRAM bytes (read + write) per launch from one ncu capture of the same
 # workload, valid while the kernel source hashes match.
+# kernel name: (DRAM bytes read + written per launch from one ncu capture (profiles/),
+#               source file of the kernel, sha1 of that file and the shared headers at
+#               capture time); an entry whose sources changed since is ignored
 NCU_TRAFFIC = {
-    # kernel name: (bytes per launch, sha1 of csrc/mp_split.cu at capture time)
+    "split_phi_project_tc": (134315264 + 3236608, "mp_split.cu", "e6f4d129ff6d0cce1abdf0afe4dce45cd55b4ffc"),
 }
+KERNEL_HEADERS = ("ptx.cuh", "mp_internal.h", "mp_errors.h")
 
 
 def log(*a):
@@ -80,9 +84,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def source_hash():
-    with open(os.path.join(ROOT, "paper_2602_02507_gb300", "csrc", "mp_split.cu"), "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()
+def source_hash(source: str):
+    """sha1 over one CUDA source file of the package and the headers it shares."""
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2602_02507_gb300", "csrc")
+    for name in (source,) + KERNEL_HEADERS:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
 
 
 # ---------------------------------------------------------------- clocks
@@ -147,11 +156,14 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle timing
-def time_oracle(w, budget_s: float, max_reps: int = 200):
+def cpu_baseline_leg(w, budget_s: float, max_reps: int = 200):
+    """The oracle on the host cores: solves of the workload for about budget_s seconds.
+    Returns (solves/s, solves, seconds, threads, Phi of the first solve); that Phi is the
+    reference the GPU paths' accuracy is stated against."""
     from oracle import oracle as O
     m = w.mesh
     tab = O.build_tables(m.r, m.theta, m.phi, m.L)
-    O.solve(tab, w.rho, m.G)  # warm caches and threads
+    phi_ref = O.solve(tab, w.rho, m.G)["phi"]  # also warms caches and threads
     reps, t0 = 0, time.perf_counter()
     while True:
         O.solve(tab, w.rho, m.G)
@@ -159,7 +171,7 @@ def time_oracle(w, budget_s: float, max_reps: int = 200):
         el = time.perf_counter() - t0
         if el >= budget_s or reps >= max_reps:
             break
-    return reps / el, reps, el, O.get_threads()
+    return reps / el, reps, el, O.get_threads(), phi_ref
 
 
 # ---------------------------------------------------------------- reference arm
@@ -195,6 +207,24 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------- multi-rank helpers
+def max_over_ranks_on(x: float, world: int, device) -> float:
+    """Largest x over the ranks of the default process group (x itself at world 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, total_ms: float) -> float:
+    """Solves per second of the whole job: every rank solves `steps` replicas of the
+    workload; the slowest rank's time (total_ms) bounds the job."""
+    return world * steps / (total_ms * 1e-3)
 
 
 # ---------------------------------------------------------------- our arm
@@ -235,11 +265,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_on(x, world, "cuda")
 
     w = W.presn()
     m = w.mesh
@@ -263,16 +289,12 @@ def run_ours(args):
     p64 = phi64.cpu().numpy()
     acc["phi_max_rel_err_split_vs_fp64_gpu"] = float(np.max(np.abs(p_split - p64) / np.abs(p64)))
     cpu = None
-    if rank == 0:
-        from oracle import oracle as O
-        tab = O.build_tables(m.r, m.theta, m.phi, m.L)
-        ref = O.solve(tab, w.rho, m.G)["phi"]
+    if rank == 0 and world == 1:
+        v, reps, el, cores, ref = cpu_baseline_leg(w, args.cpu_seconds)
+        cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": f"{reps} whole-workload solves (factored FP64 oracle, tables prebuilt) in {el:.1f} s"}
         acc["phi_max_rel_err_split_vs_oracle"] = float(np.max(np.abs(p_split - ref) / np.abs(ref)))
         acc["phi_max_rel_err_fp64_gpu_vs_oracle"] = float(np.max(np.abs(p64 - ref) / np.abs(ref)))
-        if world == 1:
-            v, reps, el, cores = time_oracle(w, args.cpu_seconds)
-            cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{reps} whole-workload solves (factored FP64 oracle, tables prebuilt) in {el:.1f} s"}
 
     # ---- timed region: split path, K solves (each one CUDA graph launch of the kernel chain)
     for _ in range(args.warmup):
@@ -296,7 +318,7 @@ def run_ours(args):
     local_ms = ev0.elapsed_time(ev1)
     total_ms = max_over_ranks(local_ms)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(world, args.steps, total_ms)
 
     # ---- per-kernel durations: the same solves launched kernel by kernel with CUDA events
     # between them on the mesh stream (events cost a little time of their own)
@@ -348,7 +370,7 @@ def run_ours(args):
     achieved = nbytes / (avg_ms * 1e-3) / 1e9
     traffic = None
     rec = NCU_TRAFFIC.get(dom)
-    if rec and rec[1] == source_hash():
+    if rec and rec[2] == source_hash(rec[1]):
         traffic = rec[0]
     kernels = {k: {"launches": v["launches"], "avg_us": 1e3 * v["total_ms"] / v["launches"],
                    "share": v["total_ms"] / sum(x["total_ms"] for x in prof.values())} for k, v in prof.items()}

@@ -364,7 +364,6 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
     m->G = G;
     m->r_ref = r_ref;
     m->prec = prec;
-    m->origin = (r_edges[0] == 0.0);
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     m->h_r.assign(r_edges, r_edges + n_r + 1);
     m->h_th.assign(theta_edges, theta_edges + n_theta + 1);

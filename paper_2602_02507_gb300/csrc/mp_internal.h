@@ -59,7 +59,6 @@ struct mp_mesh {
     long long N = 0;           // cells
     double G = 1.0, r_ref = 1.0;
     int prec = 0, eff_prec = 0;
-    int origin = 0;            // r_edges[0] == 0
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
     std::vector<double> h_r, h_th, h_ph;

@@ -14,7 +14,8 @@
 // (a doubling, exact).  The float64 pipe is narrow on this part, so the scans
 // keep float64 operations to the recurrences themselves.
 // A shell touching r = 0 uses, for l >= 2, the exact own-shell value
-// 6 r_1^2 / (5 (l+3)) A[0][q] in place of the divergent midpoint split.
+// 6 r_1^2 / (5 (l+3)) A[0][q] in place of the divergent midpoint split; the
+// tables carry it (GI at the origin shell), so the scans have no special case.
 #include "mp_internal.h"
 #include "ptx.cuh"
 
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
                                              const double *__restrict__ WI, const double *__restrict__ GR,
                                              const double *__restrict__ GI, double *__restrict__ MR,
                                              double *__restrict__ MI, double *__restrict__ C,
-                                             float *__restrict__ C32, int n_r, int KL, int origin, double r1sq)
+                                             float *__restrict__ C32, int n_r, int KL)
 {
     __shared__ double wt[2][NT / 32];
     pdl_wait();  // A comes from the previous kernel
@@ -101,14 +102,7 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
         MI[(size_t)i * KL + q] = mi;
         const double mr_lo = MR[(size_t)i * KL + q];
         const double mr_hi = fma(wr[i], a, mr_lo);
-        double c;
-        if (origin && i == 0 && l >= 2) {
-            // the own-shell value 6 r_1^2 / (5 (l+3)) A[0][q] replaces the divergent midpoint split
-            const double sself = 6.0 * r1sq / (5.0 * (l + 3.0));
-            c = 2.0 * (GR[(size_t)l * n_r] * mi_hi + (-0.5 / (2.0 * l + 1.0)) * sself * a);
-        } else {
-            c = fma(GI[(size_t)l * n_r + i], mr_lo + mr_hi, GR[(size_t)l * n_r + i] * (mi + mi_hi));
-        }
+        double c = fma(GI[(size_t)l * n_r + i], mr_lo + mr_hi, GR[(size_t)l * n_r + i] * (mi + mi_hi));
         if (m > 0) c += c;
         C[(size_t)i * KL + q] = c;
         if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(c);
@@ -122,7 +116,7 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
                                                  const double *__restrict__ WI, const double *__restrict__ GR,
                                                  const double *__restrict__ GI, double *__restrict__ MR,
                                                  double *__restrict__ MI, double *__restrict__ C,
-                                                 float *__restrict__ C32, int n_r, int KL, int origin, double r1sq)
+                                                 float *__restrict__ C32, int n_r, int KL)
 {
     __shared__ double wt[2][NT / 32];
     pdl_wait();  // A comes from the previous kernel
@@ -169,14 +163,7 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
         if (i < n_r) {
             MR[(size_t)i * KL + q] = er[k];
             MI[(size_t)i * KL + q] = ei[k];
-            double c;
-            if (origin && i == 0 && l >= 2) {
-                // the own-shell value 6 r_1^2 / (5 (l+3)) A[0][q] replaces the divergent midpoint split
-                const double sself = 6.0 * r1sq / (5.0 * (l + 3.0));
-                c = 2.0 * (g1[k] * ei[k + 1] + (-0.5 / (2.0 * l + 1.0)) * sself * a[k]);
-            } else {
-                c = fma(g2[k], er[k] + er[k + 1], g1[k] * (ei[k] + ei[k + 1]));
-            }
+            double c = fma(g2[k], er[k] + er[k + 1], g1[k] * (ei[k] + ei[k + 1]));
             if (m > 0) c += c;
             C[(size_t)i * KL + q] = c;
             if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(c);
@@ -315,13 +302,15 @@ __global__ void __launch_bounds__(1024, 1) k32_theta_pipe(const float *__restric
         for (int o = 1; o < JS; o <<= 1)
 #pragma unroll
             for (int e = 0; e < 4; ++e) part[e] += __shfl_xor_sync(0xFFFFFFFFu, part[e], o);
-        if (act && js == 0) {
+        // every lane holds the four sums; lane js writes outputs js, js + JS, ... (one float64
+        // scaling per output, not per lane)
+        if (act) {
             const int pc = (m == 0) ? 0 : 2 * m - 1;
-            Ai[l0 * l0 + pc] = scale * f32_to_f64_alu(part[0]);
-            if (m > 0) Ai[l0 * l0 + pc + 1] = scale * f32_to_f64_alu(part[1]);
-            if (l0 + 1 <= L) {
-                Ai[(l0 + 1) * (l0 + 1) + pc] = scale * f32_to_f64_alu(part[2]);
-                if (m > 0) Ai[(l0 + 1) * (l0 + 1) + pc + 1] = scale * f32_to_f64_alu(part[3]);
+            for (int e = js; e < 4; e += JS) {
+                const int l = l0 + (e >> 1), sn = e & 1;
+                if (l > L || (sn && m == 0)) continue;
+                const float v = (e == 0) ? part[0] : (e == 1) ? part[1] : (e == 2) ? part[2] : part[3];
+                Ai[l * l + pc + sn] = scale * f32_to_f64_alu(v);
             }
         }
     };
@@ -391,27 +380,27 @@ __global__ void __launch_bounds__(256) k32_theta_direct(const float *__restrict_
 }  // namespace
 
 template <int NT, int CH>
-static void scan_reg_launch(mp_mesh *m, int want_f32, double r1sq)
+static void scan_reg_launch(mp_mesh *m, int want_f32)
 {
     launch_pdl(k_scan_reg<NT, CH>, dim3(m->KL), dim3(NT), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
-               m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, m->n_r, m->KL, m->origin, r1sq);
+               m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, m->n_r, m->KL);
 }
 
 // Shells per thread CH for NT threads per moment column; false when n_r > 16 NT.
 template <int NT>
-static bool scan_reg_dispatch(mp_mesh *m, int want_f32, double r1sq)
+static bool scan_reg_dispatch(mp_mesh *m, int want_f32)
 {
     const int ch = (m->n_r + NT - 1) / NT;
     if (ch <= 1)
-        scan_reg_launch<NT, 1>(m, want_f32, r1sq);
+        scan_reg_launch<NT, 1>(m, want_f32);
     else if (ch <= 2)
-        scan_reg_launch<NT, 2>(m, want_f32, r1sq);
+        scan_reg_launch<NT, 2>(m, want_f32);
     else if (ch <= 4)
-        scan_reg_launch<NT, 4>(m, want_f32, r1sq);
+        scan_reg_launch<NT, 4>(m, want_f32);
     else if (ch <= 8)
-        scan_reg_launch<NT, 8>(m, want_f32, r1sq);
+        scan_reg_launch<NT, 8>(m, want_f32);
     else if (ch <= 16)
-        scan_reg_launch<NT, 16>(m, want_f32, r1sq);
+        scan_reg_launch<NT, 16>(m, want_f32);
     else
         return false;
     return true;
@@ -419,20 +408,18 @@ static bool scan_reg_dispatch(mp_mesh *m, int want_f32, double r1sq)
 
 cudaError_t launch_scan(mp_mesh *m, int want_f32)
 {
-    const double r1sq = m->h_r[1] * m->h_r[1];
     cudaEvent_t ev;
     prof_begin(m, "radial_scan", &ev);
     bool done;
     switch (m->plan.scan_threads) {
-    case 64: done = scan_reg_dispatch<64>(m, want_f32, r1sq); break;
-    case 256: done = scan_reg_dispatch<256>(m, want_f32, r1sq); break;
-    default: done = scan_reg_dispatch<kScanThreads>(m, want_f32, r1sq); break;
+    case 64: done = scan_reg_dispatch<64>(m, want_f32); break;
+    case 256: done = scan_reg_dispatch<256>(m, want_f32); break;
+    default: done = scan_reg_dispatch<kScanThreads>(m, want_f32); break;
     }
     if (!done)
         k_scan<kScanThreads><<<m->KL, kScanThreads, 0, m->stream>>>(m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
                                                                     m->d_MR, m->d_MI, m->d_C,
-                                                                    want_f32 ? m->d_C32 : nullptr, m->n_r, m->KL,
-                                                                    m->origin, r1sq);
+                                                                    want_f32 ? m->d_C32 : nullptr, m->n_r, m->KL);
     prof_end(m, "radial_scan", ev);
     return cudaGetLastError();
 }

@@ -90,6 +90,7 @@ struct ProjParams {
     long long R;
     int n_p, n_kc, Npad, n_tiles, ns_s, ns_o;
     int n_t, P, ldF;
+    int nacc;              // tensor-memory accumulators per tile (K chunks dealt round-robin)
     uint32_t bchunk;       // bytes of one B chunk in the table (3 terms)
     uint32_t bload;        // bytes of the terms the products read (a prefix of the chunk)
 };
@@ -122,8 +123,12 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Npad = prm.Npad;
-    const uint32_t ncols = tmem_ncols_for(2 * Npad);
-    const uint32_t acc_stride = ncols / 2;  // accumulator buffers at power-of-two column offsets
+    // per tile buffer, nacc accumulators of Npad columns: chunk it of a tile accumulates into
+    // accumulator it % nacc, which shortens every float32 accumulation chain in the tensor core
+    // nacc-fold (the epilogue adds the partials)
+    const int nacc = prm.nacc;
+    const uint32_t ncols = tmem_ncols_for(2 * nacc * Npad);
+    const uint32_t acc_stride = ncols / 2;  // tile buffers at power-of-two column offsets
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS_S; ++s) {
@@ -211,8 +216,9 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                 ok = mbar_wait(smem_u32(&acc_empty[b]), ((lt >> 1) & 1) ^ 1, abort_flag, prm.err);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)b * acc_stride;
+                const uint32_t d_buf = tmem_base + (uint32_t)b * acc_stride;
                 for (int it = 0; it < prm.n_kc; ++it, rs.next(NS_S), ro.next(NS_O)) {
+                    const uint32_t d_tmem = d_buf + (uint32_t)((it % nacc) * Npad);
                     ok = mbar_wait(smem_u32(&o_full[ro.idx]), ro.phase, abort_flag, prm.err) &&
                          mbar_wait(smem_u32(&b_full[rs.idx]), rs.phase, abort_flag, prm.err);
                     if (!ok) break;
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                             const uint64_t ad =
                                 sdesc_noswizzle(a_base + c_prod_a[pi] * A_TERM_BYTES + ks * 256, 128, SBO);
                             const uint64_t bd = sdesc_noswizzle(b_base + c_prod_b[pi] * b_term + ks * 256, 128, SBO);
-                            umma_bf16(d_tmem, ad, bd, idesc, (it | ks | pi) != 0);
+                            umma_bf16(d_tmem, ad, bd, idesc, (it >= nacc) || ((ks | pi) != 0));
                         }
                     }
                     umma_commit(smem_u32(&o_empty[ro.idx]));
@@ -264,14 +270,21 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
             float *fdst = prm.F + (size_t)ish * prm.P * prm.ldF + (grow - ish * prm.n_t);
             const int ngroups = Npad / 8;
             for (int cg = 2 * grp + half; cg < ngroups && cg * 8 < prm.P; cg += 4) {
-                uint32_t v[8];
-                tmem_ld8(tmem_base + lane_base + (uint32_t)b * acc_stride + (uint32_t)(cg * 8), v);
+                uint32_t v[4][8];
+                const uint32_t col = tmem_base + lane_base + (uint32_t)b * acc_stride + (uint32_t)(cg * 8);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    if (s < nacc) tmem_ld8(col + (uint32_t)(s * Npad), v[s]);
                 tmem_ld_wait();
                 if (grow < prm.R) {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
+                        float acc = __uint_as_float(v[0][e]);
+#pragma unroll
+                        for (int s = 1; s < 4; ++s)
+                            if (s < nacc) acc += __uint_as_float(v[s][e]);
                         const int p = cg * 8 + e;
-                        if (p < prm.P) fdst[(size_t)p * prm.ldF] = fmaf(sr, prm.colsum[p], __uint_as_float(v[e]));
+                        if (p < prm.P) fdst[(size_t)p * prm.ldF] = fmaf(sr, prm.colsum[p], acc);
                     }
                 }
             }
@@ -969,13 +982,17 @@ __global__ void k_tab_theta32(const double *__restrict__ Ith, const double *__re
     Itc[(size_t)t * ldF + j] = (float)(v / dmu[j]);
 }
 
+constexpr int kSmemLimit = 232448;  // 227 KB opt-in per block on sm_100-class parts
+
 template <int A_TERMS, int NPROD>
-cudaError_t set_smem_attrs(int proj_smem, int synth_smem)
+cudaError_t set_smem_attrs()
 {
+    // the per-function limit is shared by every mesh: set it to the part's maximum once,
+    // not to one mesh's need (a larger mesh created earlier would then fail to launch)
     cudaError_t e = cudaFuncSetAttribute(k_proj_tc<A_TERMS, NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         proj_smem);
+                                         kSmemLimit);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_synth_tc<A_TERMS, NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, synth_smem);
+    return cudaFuncSetAttribute(k_synth_tc<A_TERMS, NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
 }
 
 // B terms the products read: x3 uses b0 and b1, x6 also b2
@@ -994,7 +1011,6 @@ int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs)
     return 1024 + synth::EPI_WARPS * stg_bufs * synth::STG_BYTES + ns_a * a_stage + b_slots * bchunk + 512;
 }
 
-constexpr int kSmemLimit = 232448;  // 227 KB opt-in per block on sm_100-class parts
 
 }  // namespace
 
@@ -1051,8 +1067,8 @@ cudaError_t launch_split_tables(mp_mesh *m)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (pl.a_terms == 2)
-        return set_smem_attrs<2, 3>(pl.proj_smem, pl.synth_smem);
-    return set_smem_attrs<3, 6>(pl.proj_smem, pl.synth_smem);
+        return set_smem_attrs<2, 3>();
+    return set_smem_attrs<3, 6>();
 }
 
 cudaError_t launch_split_project(mp_mesh *m, const double *rho)
@@ -1076,6 +1092,7 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho)
     prm.ns_o = 2;
     prm.bchunk = (uint32_t)(3 * pl.Npad * proj::BK * 2);
     prm.bload = (uint32_t)(proj_b_terms(pl) * pl.Npad * proj::BK * 2);
+    prm.nacc = std::max(1, std::min(std::min(4, 256 / pl.Npad), pl.n_kc));
     const int grid = std::min(prm.n_tiles, pl.proj_ctas);
     cudaEvent_t ev;
     prof_begin(m, "split_phi_project_tc", &ev);

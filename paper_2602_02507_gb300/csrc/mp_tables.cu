@@ -146,11 +146,15 @@ __device__ double pow_diff(double x0, double x1, double p)
     return pow(x0, p) * expm1(p * log1p((x1 - x0) / x0));
 }
 
-// One thread per (l, i): radial shell integrals.  At r_0 = 0 and l >= 2 the
-// irregular integral diverges; WI and GI are stored as 0 there and the
-// recurrences treat that shell's own term separately.  GR and GI are the
+// One thread per (l, i): radial shell integrals.  GR and GI are the
 // cell-average radial factors R^R = WR/V and R^I = WI/V of Eq. (Solution)
-// times the m = 0 coefficient prefactor -1/(2 (2l+1)).
+// times the m = 0 coefficient prefactor h_l = -1/(2 (2l+1)).  At r_0 = 0 and
+// l >= 2 the irregular integral diverges: WI is stored as 0 there (the inward
+// recurrence then gives M^I_0 = M^I_1, the exported edge value without the
+// own-shell term), and GI[l][0] carries the own-shell value instead.  The
+// coefficient of that shell is 2 GR M^I_1 + 2 h_l S A with S = 6 r_1^2 /
+// (5 (l+3)); the general formula GI (M^R_0 + M^R_1) + GR (M^I_0 + M^I_1) gives
+// it when GI[l][0] = 2 h_l S / WR[l][0], since M^R_0 = 0 and M^R_1 = WR A.
 __global__ void k_radial_tables(int L, int n_r, const double *__restrict__ r, double r_ref, double *__restrict__ WR,
                                 double *__restrict__ WI, double *__restrict__ GR, double *__restrict__ GI,
                                 double *__restrict__ V)
@@ -182,7 +186,10 @@ __global__ void k_radial_tables(int L, int n_r, const double *__restrict__ r, do
     WI[(size_t)l * n_r + i] = wi;
     const double hp = -0.5 / (2.0 * l + 1.0);
     GR[(size_t)l * n_r + i] = hp * (wr / vol);
-    GI[(size_t)l * n_r + i] = hp * (wi / vol);
+    if (x0 > 0.0 || l < 2)
+        GI[(size_t)l * n_r + i] = hp * (wi / vol);
+    else
+        GI[(size_t)l * n_r + i] = 2.0 * hp * (6.0 * r1 * r1 / (5.0 * (l + 3.0))) / wr;
     if (l == 0) V[i] = vol;
 }
 

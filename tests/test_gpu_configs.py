@@ -1,0 +1,122 @@
+"""The larger workloads at full size, through the C ABI, against the FP64 CPU oracle.
+
+- log-normal precision stress, 1024 x 256 x 512, L = 32: every cell against the oracle.
+- large single solve, 2048 x 512 x 1024 (1.07e9 cells), L = 64: oracle moments of the
+  whole mesh and the potential of sampled shells (the oracle computes shells one by one).
+- 64 uneven meshes solved as one graph-launched batch: the batch equals the meshes'
+  own solves bit for bit (sampled), and the smallest instances match the oracle.
+
+Phi errors are max_c |dPhi_c| / |Phi_c| (pointwise; the max-norm error max |dPhi| /
+max |Phi| is printed beside it for the large mesh).  Per-degree moment errors are
+printed for the record.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import per_l_errors, phi_rel_err
+from paper_2602_02507_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _solve(w, prec, rho_dev=None, shells=None):
+    """Phi (whole mesh, or the listed shells) and the angular moments of one GPU solve."""
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    m = w.mesh
+    rho = rho_dev if rho_dev is not None else torch.from_numpy(np.ascontiguousarray(w.rho)).cuda()
+    phi = torch.empty_like(rho)
+    n_r, K = m.shape[0], m.KL
+    A = torch.empty(n_r * K, dtype=torch.float64, device="cuda")
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=prec) as mesh:
+        mesh.set_density(rho)
+        mesh.set_phi_output(phi)
+        mesh.solve()
+        mesh.get_moments(A, None, None)
+        mesh.synchronize()
+        eff = mesh.info()["effective_precision"]
+    out = phi if shells is None else phi[shells]
+    return out.cpu().numpy(), A.cpu().numpy().reshape(n_r, K), eff
+
+
+def test_lognormal_full_size_1024x256x512_L32():
+    from oracle import oracle as O
+    w = W.lognormal()
+    m = w.mesh
+    ref = O.solve(O.build_tables(m.r, m.theta, m.phi, m.L), w.rho, m.G)
+    for prec, tol in (("fp64", 1e-12), ("bf16x3", 1e-6), ("bf16x6", 1e-6)):
+        phi, A, eff = _solve(w, prec)
+        assert eff == {"fp64": 0, "bf16x3": 1, "bf16x6": 2}[prec]
+        err = phi_rel_err(phi, ref["phi"])
+        print(f"lognormal {prec}: phi {err:.3e}, per-l A max {max(per_l_errors(A, ref['A'], m.L)):.3e}")
+        assert err <= tol, (prec, err)
+
+
+def test_large_full_size_2048x512x1024_L64_sampled_shells():
+    from oracle import oracle as O
+    w = W.large(materialize=True)
+    m = w.mesh
+    tab = O.build_tables(m.r, m.theta, m.phi, m.L)
+    ref = O.solve(tab, w.rho, m.G, want_phi=False)
+    shells = [0, 1, 700, 1400, 2046, 2047]
+    ref_phi = O.potential_shells(tab, ref["C"], shells)
+    import torch
+    rho = torch.from_numpy(w.rho).cuda()
+    del w
+    for prec in ("fp64", "bf16x3"):
+        phi, A, _ = _solve(W.large(), prec, rho_dev=rho, shells=shells)
+        pointwise = phi_rel_err(phi, ref_phi)
+        maxnorm = float(np.abs(phi - ref_phi).max() / np.abs(ref_phi).max())
+        mono = float(np.max(np.abs(A[:, 0] - ref["A"][:, 0]) / np.abs(ref["A"][:, 0])))
+        print(f"large {prec}: phi pointwise {pointwise:.3e}, max-norm {maxnorm:.3e}, A_00 {mono:.3e}")
+        assert pointwise <= (1e-12 if prec == "fp64" else 1e-6), (prec, pointwise, maxnorm, mono)
+        torch.cuda.empty_cache()
+
+
+def test_batch_of_64_uneven_meshes():
+    import torch
+    from oracle import oracle as O
+    from paper_2602_02507_gb300 import multipole as mpl
+    draws = W.batch_draws()
+    meshes, rhos, phis = [], [], []
+    for n in range(len(draws)):
+        w = W.batch_instance(n, draws)
+        m = w.mesh
+        rho = torch.from_numpy(w.rho).cuda()
+        phi = torch.empty_like(rho)
+        ms = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3")
+        ms.set_density(rho)
+        ms.set_phi_output(phi)
+        meshes.append(ms)
+        rhos.append(rho)
+        phis.append(phi)
+    b = mpl.Batch(meshes)
+    b.solve()
+    torch.cuda.synchronize()
+    batch_phi = {n: phis[n].cpu().numpy() for n in range(0, len(draws), 8)}
+    # the meshes' own solves give the same bits
+    for n in batch_phi:
+        meshes[n].solve()
+        meshes[n].synchronize()
+        assert np.array_equal(phis[n].cpu().numpy(), batch_phi[n]), n
+    b.close()
+    # the smallest instances against the oracle
+    order = sorted(range(len(draws)), key=lambda n: np.prod(draws[n][0]) * draws[n][1])
+    for n in order[:3]:
+        w = W.batch_instance(n, draws)
+        m = w.mesh
+        ref = O.solve(O.build_tables(m.r, m.theta, m.phi, m.L), w.rho, m.G)
+        err = phi_rel_err(phis[n].cpu().numpy(), ref["phi"])
+        print(f"batch instance {n} {draws[n][0]} L={draws[n][1]}: phi {err:.3e}")
+        assert err <= 1e-6, (n, err)
+    for ms in meshes:
+        ms.close()

@@ -45,6 +45,9 @@ FP64_CASES = {
     "axisymmetric_nphi1": _axisym,
     "one_polar_cell": _one_polar_cell,
     "presn_64x32x64_L16": lambda: W.presn(n_r=64, n_theta=32, n_phi=64, L=16),
+    # more shells than the register-resident scan holds (16 per thread x 128 threads): the
+    # general chunked scan
+    "long_radial_2100x2x4_L3": lambda: W.random_small((2100, 2, 4), 3, seed=9, r0=1.0, r1=2.0),
 }
 
 
@@ -71,6 +74,10 @@ SPLIT_CASES = {
                                    ("bf16x3", "bf16x6")),
     "monopole_L0_8x16x32": (lambda: W.presn(n_r=8, n_theta=16, n_phi=32, L=0), ("bf16x3",)),
     "random_rough_6x32x64_L8": (lambda: W.random_small((6, 32, 64), 8, seed=8, r0=0.2, r1=1.0), ("bf16x6",)),
+    # tables too large for shared memory: the direct theta contraction and the per-row
+    # theta synthesis
+    "high_L_fallback_4x96x64_L30": (lambda: W.presn(n_r=4, n_theta=96, n_phi=64, L=30, r_lo=1e7, r_hi=1.3e7),
+                                    ("bf16x3",)),
 }
 
 
