@@ -774,14 +774,15 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
         std::string line;
         while (std::getline(f, line)) {
             std::istringstream is(line);
-            int a, b, c, d, e, ns_s, ns_b, sw;
-            if (is >> a >> b >> c >> d >> e >> ns_s >> ns_b >> sw) {
+            int a, b, c, d, e, ns_s, ns_b, sw, br;
+            if (is >> a >> b >> c >> d >> e >> ns_s >> ns_b >> sw >> br) {
                 std::ostringstream k;
                 k << a << ' ' << b << ' ' << c << ' ' << d << ' ' << e;
                 if (k.str() == key) {
                     m->plan.ns_s = ns_s;
                     m->plan.ns_b = ns_b;
                     m->plan.scan_threads = sw;
+                    m->plan.proj_b_resident = br ? m->plan.proj_res_ok : !m->plan.proj_ring_ok;
                     drop_graph(m);
                     return MP_OK;
                 }
@@ -796,16 +797,18 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     }
     const SplitPlan base = m->plan;
     struct Cand {
-        int ns_s, ns_b, sw;
+        int ns_s, ns_b, sw, br;
     };
     std::vector<Cand> cands;
     const int sws[] = {64, 128, 256};
     if (m->eff_prec == MP_PREC_FP64) {
-        for (int sw : sws) cands.push_back({base.ns_s, base.ns_b, sw});
+        for (int sw : sws) cands.push_back({base.ns_s, base.ns_b, sw, 0});
     } else {
         for (int ns_s = 3; ns_s <= base.ns_s; ++ns_s)
             for (int ns_b = 2; ns_b <= base.ns_b; ++ns_b)
-                for (int sw : sws) cands.push_back({ns_s, ns_b, sw});
+                for (int br = 0; br <= 1; ++br)
+                    if (br ? base.proj_res_ok : base.proj_ring_ok)
+                        for (int sw : sws) cands.push_back({ns_s, ns_b, sw, br});
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -813,12 +816,13 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     const int saved_prof = m->profiling;
     m->profiling = 0;
     float best = FLT_MAX;
-    Cand best_c = {base.ns_s, base.ns_b, base.scan_threads};
+    Cand best_c = {base.ns_s, base.ns_b, base.scan_threads, base.proj_b_resident};
     mp_status st = MP_OK;
     for (const Cand &c : cands) {
         m->plan.ns_s = c.ns_s;
         m->plan.ns_b = c.ns_b;
         m->plan.scan_threads = c.sw;
+        m->plan.proj_b_resident = c.br;
         st = run_solve(m, m->rho, phi);  // warm-up
         if (st != MP_OK) break;
         cudaEventRecord(e0, m->stream);
@@ -844,6 +848,7 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     m->plan.ns_s = best_c.ns_s;
     m->plan.ns_b = best_c.ns_b;
     m->plan.scan_threads = best_c.sw;
+    m->plan.proj_b_resident = best_c.br;
     drop_graph(m);
     if (st != MP_OK) {
         m->plan = base;
@@ -851,7 +856,7 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     }
     if (cache_path) {
         std::ofstream f(cache_path, std::ios::app);
-        f << key << ' ' << best_c.ns_s << ' ' << best_c.ns_b << ' ' << best_c.sw << '\n';
+        f << key << ' ' << best_c.ns_s << ' ' << best_c.ns_b << ' ' << best_c.sw << ' ' << best_c.br << '\n';
     }
     return mp_mesh_synchronize(m);
 }

@@ -37,6 +37,8 @@ struct SplitPlan {
     int proj_smem = 0;    // dynamic shared memory bytes
     int synth_smem = 0;
     int ns_s = 6;         // projection: TMA stages of the density
+    int proj_b_resident = 0;  // projection: whole pre-split table held in shared memory
+    int proj_res_ok = 0, proj_ring_ok = 0;  // projection: which table modes fit the reserved memory
     int ns_b = 3;         // synthesis: table stages (when not resident)
     int ns_a = 2;         // synthesis: A-operand stages
     int b_resident = 0;   // synthesis: whole table held in shared memory

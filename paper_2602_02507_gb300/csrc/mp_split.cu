@@ -91,6 +91,8 @@ struct ProjParams {
     int n_p, n_kc, Npad, n_tiles, ns_s, ns_o;
     int n_t, P, ldF;
     int nacc;              // tensor-memory accumulators per tile (K chunks dealt round-robin)
+    int b_resident;        // 1: every table chunk stays in shared memory for the whole launch
+    int ns_b;              // table ring slots (when not resident)
     uint32_t bchunk;       // bytes of one B chunk in the table (3 terms)
     uint32_t bload;        // bytes of the terms the products read (a prefix of the chunk)
 };
@@ -109,14 +111,14 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
     using namespace proj;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int NS_S = prm.ns_s, NS_O = prm.ns_o;
+    const int NS_S = prm.ns_s, NS_O = prm.ns_o, NS_B = prm.ns_b;
     uint8_t *sS = smem;
-    uint8_t *sB = sS + (size_t)NS_S * S_BYTES;
-    uint8_t *sA = sB + (size_t)NS_S * prm.bload;
+    uint8_t *sB = sS + (size_t)NS_S * S_BYTES;                        // table: n_kc chunks or NS_B slots
+    uint8_t *sA = sB + (size_t)(prm.b_resident ? prm.n_kc : NS_B) * prm.bload;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sA + (size_t)NS_O * A_TERMS * A_TERM_BYTES);
     uint64_t *s_full = bars, *s_empty = bars + NS_S;
-    uint64_t *b_full = bars + 2 * NS_S, *b_empty = b_full + NS_S;
-    uint64_t *o_full = bars + 4 * NS_S, *o_empty = o_full + NS_O;
+    uint64_t *b_full = bars + 2 * NS_S, *b_empty = b_full + NS_B;
+    uint64_t *o_full = b_empty + NS_B, *o_empty = o_full + NS_O;
     uint64_t *acc_full = o_empty + NS_O, *acc_empty = acc_full + 2, *drain = acc_empty + 2;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
@@ -134,6 +136,8 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         for (int s = 0; s < NS_S; ++s) {
             mbar_init(smem_u32(&s_full[s]), 1);
             mbar_init(smem_u32(&s_empty[s]), kGroupWarps);  // density stages: free once converted
+        }
+        for (int s = 0; s < NS_B; ++s) {
             mbar_init(smem_u32(&b_full[s]), 1);
             mbar_init(smem_u32(&b_empty[s]), 1);            // table stages: free once the MMAs read them
         }
@@ -148,6 +152,13 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         mbar_init(smem_u32(drain), 1);
         *abort_flag = 0;
         fence_mbar_init();
+        if (prm.b_resident && (int)blockIdx.x < prm.n_tiles) {
+            // the whole (static) table once, ahead of the wait for the previous kernel
+            mbar_arrive_expect_tx(smem_u32(&b_full[0]), (uint32_t)prm.n_kc * prm.bload);
+            for (int kc = 0; kc < prm.n_kc; ++kc)
+                bulk_load(smem_u32(sB + (size_t)kc * prm.bload), prm.tabB + (size_t)kc * prm.bchunk, prm.bload,
+                          smem_u32(&b_full[0]));
+        }
     }
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_holder), ncols);
@@ -157,8 +168,8 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
-    // barrier set-up and tensor memory overlap the previous kernel's tail; the density and
-    // the outputs are touched only after the previous kernel has completed
+    // barrier set-up, tensor memory and the table copy overlap the previous kernel's tail;
+    // the density and the outputs are touched only after the previous kernel has completed
     pdl_trigger();
     pdl_wait();
 
@@ -166,8 +177,10 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         // ---------------- producer: two TMA boxes of rho, and the table chunk on its own ring
         if (lane == 0) {
             tma_prefetch_desc(&tmS);
-            Ring rs;
-            int issued = 0;
+            // rho is read once per solve: its lines go first, ahead of F, tables and moments
+            const uint64_t l2_first = l2_evict_first_policy();
+            Ring rs, rb;
+            int issued = 0, issued_b = 0;
             for (int tile = blockIdx.x; tile < prm.n_tiles && !*abort_flag; tile += gridDim.x) {
                 for (int it = 0; it < prm.n_kc; ++it, rs.next(NS_S)) {
                     const int kc = rotated_chunk(it, tile, prm.n_kc);
@@ -176,17 +189,17 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                     const bool two = kc * BK + 16 < prm.n_p;  // the second box holds cells
                     mbar_arrive_expect_tx(fb, two ? S_BYTES : BOX_BYTES);
                     const uint32_t dst = smem_u32(sS + (size_t)rs.idx * S_BYTES);
-                    tma_load_2d(dst, &tmS, fb, kc * BK, tile * kBM);
-                    if (two) tma_load_2d(dst + BOX_BYTES, &tmS, fb, kc * BK + 16, tile * kBM);
-                    if (!mbar_wait(smem_u32(&b_empty[rs.idx]), rs.phase ^ 1, abort_flag, prm.err)) {
-                        ++issued;
-                        break;
-                    }
-                    const uint32_t bb = smem_u32(&b_full[rs.idx]);
-                    mbar_arrive_expect_tx(bb, prm.bload);
-                    bulk_load(smem_u32(sB + (size_t)rs.idx * prm.bload), prm.tabB + (size_t)kc * prm.bchunk,
-                              prm.bload, bb);
+                    tma_load_2d_hint(dst, &tmS, fb, kc * BK, tile * kBM, l2_first);
+                    if (two) tma_load_2d_hint(dst + BOX_BYTES, &tmS, fb, kc * BK + 16, tile * kBM, l2_first);
                     ++issued;
+                    if (prm.b_resident) continue;
+                    if (!mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err)) break;
+                    const uint32_t bb = smem_u32(&b_full[rb.idx]);
+                    mbar_arrive_expect_tx(bb, prm.bload);
+                    bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bload), prm.tabB + (size_t)kc * prm.bchunk,
+                              prm.bload, bb);
+                    ++issued_b;
+                    rb.next(NS_B);
                 }
             }
             if (*abort_flag && issued > 0) {
@@ -196,10 +209,23 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                     back.idx = (back.idx == 0) ? NS_S - 1 : back.idx - 1;
                     if (back.idx == NS_S - 1) back.phase ^= 1u;
                     const long long t0 = clock64();
-                    while ((!mbar_try_wait(smem_u32(&s_full[back.idx]), back.phase) ||
-                            !mbar_try_wait(smem_u32(&b_full[back.idx]), back.phase)) &&
+                    while (!mbar_try_wait(smem_u32(&s_full[back.idx]), back.phase) &&
                            clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
                     }
+                }
+                Ring bback = rb;
+                for (int n = 0; n < NS_B && n < issued_b; ++n) {
+                    bback.idx = (bback.idx == 0) ? NS_B - 1 : bback.idx - 1;
+                    if (bback.idx == NS_B - 1) bback.phase ^= 1u;
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(smem_u32(&b_full[bback.idx]), bback.phase) &&
+                           clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
+                    }
+                }
+            }
+            if (*abort_flag && prm.b_resident) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(smem_u32(&b_full[0]), 0) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
                 }
             }
         }
@@ -208,23 +234,25 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(kBM, Npad);
             const uint32_t b_term = (uint32_t)Npad * (BK * 2);
-            Ring rs, ro;
+            Ring ro, rb;
             int lt = 0;
             bool ok = true;
+            if (prm.b_resident && (int)blockIdx.x < prm.n_tiles) ok = mbar_wait(smem_u32(&b_full[0]), 0, abort_flag, prm.err);
             for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ++lt) {
                 const int b = lt & 1;
                 ok = mbar_wait(smem_u32(&acc_empty[b]), ((lt >> 1) & 1) ^ 1, abort_flag, prm.err);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t d_buf = tmem_base + (uint32_t)b * acc_stride;
-                for (int it = 0; it < prm.n_kc; ++it, rs.next(NS_S), ro.next(NS_O)) {
+                for (int it = 0; it < prm.n_kc; ++it, ro.next(NS_O)) {
                     const uint32_t d_tmem = d_buf + (uint32_t)((it % nacc) * Npad);
                     ok = mbar_wait(smem_u32(&o_full[ro.idx]), ro.phase, abort_flag, prm.err) &&
-                         mbar_wait(smem_u32(&b_full[rs.idx]), rs.phase, abort_flag, prm.err);
+                         (prm.b_resident || mbar_wait(smem_u32(&b_full[rb.idx]), rb.phase, abort_flag, prm.err));
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t a_base = smem_u32(sA + (size_t)ro.idx * A_TERMS * A_TERM_BYTES);
-                    const uint32_t b_base = smem_u32(sB + (size_t)rs.idx * prm.bload);
+                    const int bslot = prm.b_resident ? rotated_chunk(it, tile, prm.n_kc) : rb.idx;
+                    const uint32_t b_base = smem_u32(sB + (size_t)bslot * prm.bload);
 #pragma unroll
                     for (int ks = 0; ks < BK / 16; ++ks) {
 #pragma unroll
@@ -236,7 +264,10 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                         }
                     }
                     umma_commit(smem_u32(&o_empty[ro.idx]));
-                    umma_commit(smem_u32(&b_empty[rs.idx]));
+                    if (!prm.b_resident) {
+                        umma_commit(smem_u32(&b_empty[rb.idx]));
+                        rb.next(NS_B);
+                    }
                 }
                 if (!ok) break;
                 umma_commit(smem_u32(&acc_full[b]));
@@ -295,14 +326,20 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         };
 
         // this thread converts cells [16 half, 16 half + 16) of its group's stages: box `half`
+        // reference value of a row: its first cell, read directly (both groups need it); the
+        // next tile's is requested one tile ahead, so its HBM latency hides behind this tile
+        auto load_ref = [&](int tile) -> uint2 {
+            uint2 v = make_uint2(0u, 0u);
+            const long long grow = (long long)tile * kBM + row;
+            if (tile < prm.n_tiles && grow < prm.R) v = __ldg(reinterpret_cast<const uint2 *>(prm.rho + grow * prm.n_p));
+            return v;
+        };
+        uint2 ref_next = load_ref(blockIdx.x);
         for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ++lt) {
-            // reference value of the row: its first cell, read directly (both groups need it)
             {
-                const long long grow = (long long)tile * kBM + row;
-                uint2 v0 = make_uint2(0u, 0u);
-                if (grow < prm.R) v0 = __ldg(reinterpret_cast<const uint2 *>(prm.rho + grow * prm.n_p));
                 uint32_t e0;
-                sref = f64w_to_f32_fast(v0.x, v0.y, e0);
+                sref = f64w_to_f32_fast(ref_next.x, ref_next.y, e0);
+                ref_next = load_ref(tile + gridDim.x);
             }
             for (int it = 0; it < prm.n_kc; ++it, ++c) {
                 if ((int)(c & 1) != grp) continue;
@@ -832,6 +869,9 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
         const int cw = warp - 2, qd = warp & 3, quarter = cw >> 2;
         const int row = qd * 32 + lane;
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+        // Phi is written once per solve: its lines leave L2 first (written back now, not
+        // during the next solve's density stream)
+        const uint64_t l2_first = l2_evict_first_policy();
         Ring ra;
         uint32_t u = 0, cs = 0;
         bool ok = true;
@@ -850,11 +890,17 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                 tc_fence_after();
                 const uint32_t tcol = tmem_base + lane_base + (uint32_t)buf * acc_stride;
                 const int nmine = (NC / 16 - quarter + 3) / 4;  // chunks quarter, quarter + 4, ...
+                // the next chunk's accumulators are requested before this chunk is converted
+                uint32_t vn[16];
+                if (nmine > 0) tmem_ld16(tcol + (uint32_t)((quarter + 4 * rotated_chunk(0, tile, nmine)) * 16), vn);
                 for (int it = 0; it < nmine; ++it) {
                     const int ch = quarter + 4 * rotated_chunk(it, tile, nmine);
                     uint32_t v[16];
-                    tmem_ld16(tcol + (uint32_t)(ch * 16), v);
                     tmem_ld_wait();
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] = vn[e];
+                    if (it + 1 < nmine)
+                        tmem_ld16(tcol + (uint32_t)((quarter + 4 * rotated_chunk(it + 1, tile, nmine)) * 16), vn);
                     uint8_t *st = stg + (size_t)(cw * NSTG + (cs % NSTG)) * STG_BYTES;
                     ++cs;
                     if (lane == 0) {
@@ -875,7 +921,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0 && box_valid) {
-                        tma_store_2d(&tmPhi, smem_u32(st), nc * NC + ch * 16, (int)box_row);
+                        tma_store_2d_hint(&tmPhi, smem_u32(st), nc * NC + ch * 16, (int)box_row, l2_first);
                         bulk_commit();
                     }
                 }
@@ -998,10 +1044,14 @@ cudaError_t set_smem_attrs()
 // B terms the products read: x3 uses b0 and b1, x6 also b2
 int proj_b_terms(const SplitPlan &pl) { return pl.n_products == 3 ? 2 : 3; }
 
-int proj_smem_bytes(const SplitPlan &pl, int ns_s, int ns_o)
+// The table ring (when the table is not resident) is as deep as the density ring: both
+// loads of a chunk come from one thread, so a shallower table ring would cap the density
+// prefetch depth.
+int proj_smem_bytes(const SplitPlan &pl, int ns_s, int ns_o, int b_resident)
 {
     const int bload = proj_b_terms(pl) * pl.Npad * proj::BK * 2;
-    return 1024 + ns_s * proj::S_BYTES + ns_s * bload + ns_o * pl.a_terms * proj::A_TERM_BYTES + 512;
+    return 1024 + ns_s * proj::S_BYTES + (b_resident ? pl.n_kc : ns_s) * bload +
+           ns_o * pl.a_terms * proj::A_TERM_BYTES + 512;
 }
 
 int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs)
@@ -1018,9 +1068,17 @@ int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs)
 int split_smem_limits(mp_mesh *m)
 {
     SplitPlan &pl = m->plan;
-    int ns_s = 4;
-    while (ns_s > 2 && proj_smem_bytes(pl, ns_s, 2) > kSmemLimit) --ns_s;
-    if (proj_smem_bytes(pl, ns_s, 2) > kSmemLimit) return 1;
+    // projection: four density stages (more measured no faster), the table resident when it
+    // fits beside them, else a ring; fewer stages when neither fits
+    int ns_s = 0, b_res = 0;
+    for (int s = 4; s >= 2 && ns_s == 0; --s)
+        for (int r = 1; r >= 0; --r)
+            if (proj_smem_bytes(pl, s, 2, r) <= kSmemLimit) {
+                ns_s = s;
+                b_res = r;
+                break;
+            }
+    if (ns_s == 0) return 1;
     // synthesis: prefer the whole table resident, two A stages and double-buffered staging
     const int n_chunks = pl.n_nc * (pl.Kpad / 16);
     struct Cfg {
@@ -1041,8 +1099,13 @@ int split_smem_limits(mp_mesh *m)
         }
     }
     if (!found) return 2;
-    pl.proj_smem = proj_smem_bytes(pl, ns_s, 2);
     pl.ns_s = ns_s;
+    pl.proj_b_resident = b_res;
+    pl.proj_res_ok = proj_smem_bytes(pl, ns_s, 2, 1) <= kSmemLimit;
+    pl.proj_ring_ok = proj_smem_bytes(pl, ns_s, 2, 0) <= kSmemLimit;
+    // the launch reserves the larger of the table modes that fit, so the tuner may switch them
+    pl.proj_smem = std::max(pl.proj_res_ok ? proj_smem_bytes(pl, ns_s, 2, 1) : 0,
+                            pl.proj_ring_ok ? proj_smem_bytes(pl, ns_s, 2, 0) : 0);
     return 0;
 }
 
@@ -1093,6 +1156,8 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho)
     prm.bchunk = (uint32_t)(3 * pl.Npad * proj::BK * 2);
     prm.bload = (uint32_t)(proj_b_terms(pl) * pl.Npad * proj::BK * 2);
     prm.nacc = std::max(1, std::min(std::min(4, 256 / pl.Npad), pl.n_kc));
+    prm.b_resident = pl.proj_b_resident;
+    prm.ns_b = pl.ns_s;
     const int grid = std::min(prm.n_tiles, pl.proj_ctas);
     cudaEvent_t ev;
     prof_begin(m, "split_phi_project_tc", &ev);
