@@ -154,7 +154,7 @@ static void free_mesh_buffers(mp_mesh *m)
 {
     void *ptrs[] = {m->d_r,   m->d_Ith,  m->d_dmu,    m->d_Iph,   m->d_Iphc,   m->d_WR,    m->d_WI,
                     m->d_GR,  m->d_GI,   m->d_V,      m->d_A,     m->d_MR,     m->d_MI,    m->d_C,
-                    m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_Ith32, m->d_Itc32, m->d_colsum,
+                    m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_Ith32, m->d_Itc32, m->d_Itc0, m->d_C0, m->d_colsum,
                     m->d_tabB, m->d_tabT, m->d_Aop, m->d_G0, m->phi_own, m->rho_stage, m->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -417,6 +417,8 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
         ALLOC(m->d_C32, (size_t)n_r * m->KL);
         ALLOC(m->d_Ith32, (size_t)m->T * pl.ldF);
         ALLOC(m->d_Itc32, (size_t)m->T * pl.ldF);
+        ALLOC(m->d_Itc0, (size_t)(l_max + 1) * n_theta);
+        ALLOC(m->d_C0, (size_t)n_r * (l_max + 1));
         ALLOC(m->d_colsum, pl.Npad);
         m->tabB_chunk_bytes = (size_t)3 * pl.Npad * 64;
         m->tabT_chunk_bytes = (size_t)3 * pl.NC * 32;
@@ -425,10 +427,10 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
         {
             const size_t tiles = (size_t)((m->R + 127) / 128);
             ALLOC(m->d_Aop, tiles * pl.a_terms * 128 * pl.Kpad * 2);
-            ALLOC(m->d_G0, tiles * 128);
+            ALLOC(m->d_G0, tiles * 256);
             // rows past the last one in the final tile are never written by the theta synthesis
             cudaMemsetAsync(m->d_Aop, 0, tiles * pl.a_terms * 128 * pl.Kpad * 2, m->stream);
-            cudaMemsetAsync(m->d_G0, 0, tiles * 128 * sizeof(float), m->stream);
+            cudaMemsetAsync(m->d_G0, 0, tiles * 256 * sizeof(float), m->stream);
             // padding cells of the polar rows stay zero: the theta contraction sums over them
             cudaMemsetAsync(m->d_F32, 0, (size_t)n_r * m->P * pl.ldF * sizeof(float), m->stream);
             cudaMemsetAsync(m->d_Ith32, 0, (size_t)m->T * pl.ldF * sizeof(float), m->stream);

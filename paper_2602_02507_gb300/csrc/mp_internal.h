@@ -93,7 +93,9 @@ struct mp_mesh {
     float *d_Itc32 = nullptr;     // [T][n_t]   Ith / dmu, float
     float *d_colsum = nullptr;    // [Npad]     sum_k Iph[p][k]
     uint8_t *d_Aop = nullptr;     // synthesis A operand, bf16 terms per 128-row tile, canonical layout
-    float *d_G0 = nullptr;        // [tiles * 128] m = 0 column of the theta synthesis
+    float *d_G0 = nullptr;        // [tiles * 128] x (hi, lo) float pairs: m = 0 column of the theta synthesis
+    float2 *d_Itc0 = nullptr;     // [L+1][n_t] Ith[tri(l,0)][j] / dmu_j as (hi, lo) float pairs
+    float2 *d_C0 = nullptr;       // [n_r][L+1] m = 0 coefficients C[i][l^2] as (hi, lo) float pairs
     uint8_t *d_tabB = nullptr;    // projection B operand, bf16 x 3 terms, canonical layout
     uint8_t *d_tabT = nullptr;    // synthesis B operand, bf16 x 3 terms, canonical layout
     size_t tabB_chunk_bytes = 0, tabT_chunk_bytes = 0;

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
                                              const double *__restrict__ WI, const double *__restrict__ GR,
                                              const double *__restrict__ GI, double *__restrict__ MR,
                                              double *__restrict__ MI, double *__restrict__ C,
-                                             float *__restrict__ C32, int n_r, int KL)
+                                             float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL)
 {
     __shared__ double wt[2][NT / 32];
     pdl_wait();  // A comes from the previous kernel
@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
     while ((l + 1) * (l + 1) <= q) ++l;
     const int p = q - l * l;
     const int m = pcol_m(p);
+    const int Lp1 = (int)sqrtf((float)KL + 0.5f);  // L + 1
     const int chunk = (n_r + NT - 1) / NT;
     const int i0 = min(n_r, (int)threadIdx.x * chunk), i1 = min(n_r, i0 + chunk);
     const double *wr = WR + (size_t)l * n_r;
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
         if (m > 0) c += c;
         C[(size_t)i * KL + q] = c;
         if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(c);
+        if (C0 && p == 0) C0[(size_t)i * Lp1 + l] = f32_pair(c);
     }
 }
 
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
                                                  const double *__restrict__ WI, const double *__restrict__ GR,
                                                  const double *__restrict__ GI, double *__restrict__ MR,
                                                  double *__restrict__ MI, double *__restrict__ C,
-                                                 float *__restrict__ C32, int n_r, int KL)
+                                                 float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL)
 {
     __shared__ double wt[2][NT / 32];
     pdl_wait();  // A comes from the previous kernel
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
     while ((l + 1) * (l + 1) <= q) ++l;
     const int p = q - l * l;
     const int m = pcol_m(p);
+    const int Lp1 = (int)sqrtf((float)KL + 0.5f);  // L + 1
     const int i0 = (int)threadIdx.x * CH;
     const double *wr = WR + (size_t)l * n_r;
     const double *wi = WI + (size_t)l * n_r;
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
             if (m > 0) c += c;
             C[(size_t)i * KL + q] = c;
             if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(c);
+            if (C0 && p == 0) C0[(size_t)i * Lp1 + l] = f32_pair(c);
         }
     }
     if (threadIdx.x == NT - 1) {
@@ -347,33 +351,88 @@ __global__ void __launch_bounds__(1024, 1) k32_theta_pipe(const float *__restric
     }
 }
 
-// Same sums for meshes whose table and rows do not fit in shared memory: block
-// i, thread per (l, m) pair, table and rows read through L1.
-__global__ void __launch_bounds__(256) k32_theta_direct(const float *__restrict__ F, const float *__restrict__ Ith,
-                                                        double *__restrict__ A, int n_t, int L, int KL, int T, int P,
-                                                        int ldF, double scale)
+// Same sums for tables and shells that exceed shared memory, as one GEMM per order m:
+//   Out_m[l][col] = sum_j Ith[tri(l,m)][j] F[i(col)][p(col)][j],  l = m..L,
+//   col = (shell i, cos | sin).
+// Block (tile of kMgShells shells, m) computes a 64 x 64 tile (degrees x columns; more
+// degree tiles in turn when L + 1 - m > 64) in K chunks of kMgK polar cells: the
+// chunk's table rows and F rows pass through shared memory (coalesced float4 loads);
+// thread (rg, cg) owns degrees rg + 16 a and columns cg + 16 b (a, b < 4), so the eight
+// lanes of a shared-memory phase read eight different banks.  Products are summed in
+// float32 over blocks of eight cells, block sums with Kahan compensation.
+constexpr int kMgShells = 32, kMgCols = 2 * kMgShells, kMgRows = 64, kMgK = 32, kMgLd = kMgK + 4;
+
+__global__ void __launch_bounds__(256) k32_theta_mgemm(const float *__restrict__ F, const float *__restrict__ Ith,
+                                                       double *__restrict__ A, int n_r, int n_t, int L, int KL, int P,
+                                                       int ldF, double scale)
 {
-    const int i = blockIdx.x;
-    const float *fr = F + (size_t)i * P * ldF;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        int l = 0;
-        while ((l + 1) * (l + 2) / 2 <= t) ++l;
-        const int m = t - l * (l + 1) / 2;
-        const int pc = (m == 0) ? 0 : 2 * m - 1;
-        const float *tr = Ith + (size_t)t * ldF, *fc = fr + (size_t)pc * ldF, *fs = fr + (size_t)(pc + 1) * ldF;
-        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
-        for (int j0 = 0; j0 < n_t; j0 += 8) {
-            float b0 = 0.f, b1 = 0.f;
-            for (int j = j0; j < min(n_t, j0 + 8); ++j) {
-                const float w = __ldg(tr + j);
-                b0 = fmaf(w, __ldg(fc + j), b0);
-                if (m > 0) b1 = fmaf(w, __ldg(fs + j), b1);
+    __shared__ __align__(16) float sT[kMgRows][kMgLd];
+    __shared__ __align__(16) float sF[kMgCols][kMgLd];
+    pdl_wait();  // F comes from the previous kernel
+    const int m = blockIdx.y, i0 = blockIdx.x * kMgShells;
+    const int nl = L + 1 - m;
+    const int pc = (m == 0) ? 0 : 2 * m - 1;
+    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+    for (int l0 = 0; l0 < nl; l0 += kMgRows) {
+        float s[4][4], c[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) s[a][b] = c[a][b] = 0.0f;
+        for (int j0 = 0; j0 < n_t; j0 += kMgK) {
+            __syncthreads();  // the previous chunk is consumed
+            for (int e = tid; e < kMgRows * (kMgK / 4); e += blockDim.x) {
+                const int r = e >> 3, q = e & 7, j = j0 + 4 * q;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (l0 + r < nl && j < ldF) v = *reinterpret_cast<const float4 *>(Ith + (size_t)tri(m + l0 + r, m) * ldF + j);
+                *reinterpret_cast<float4 *>(&sT[r][4 * q]) = v;
             }
-            kahan_add(s0, c0, b0);
-            kahan_add(s1, c1, b1);
+            for (int e = tid; e < kMgCols * (kMgK / 4); e += blockDim.x) {
+                const int col = e >> 3, q = e & 7, j = j0 + 4 * q;
+                const int i = i0 + (col >> 1), sn = col & 1;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < n_r && j < ldF && (sn == 0 || m > 0))
+                    v = *reinterpret_cast<const float4 *>(F + ((size_t)i * P + pc + sn) * ldF + j);
+                *reinterpret_cast<float4 *>(&sF[col][4 * q]) = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int jb = 0; jb < kMgK; jb += 8) {
+                float blk[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) blk[a][b] = 0.0f;
+#pragma unroll
+                for (int jj = jb; jj < jb + 8; jj += 4) {
+                    float4 t[4], f[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) t[a] = *reinterpret_cast<const float4 *>(&sT[rg + 16 * a][jj]);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) f[b] = *reinterpret_cast<const float4 *>(&sF[cg + 16 * b][jj]);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) blk[a][b] = dot4(t[a], f[b], blk[a][b]);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) kahan_add(s[a][b], c[a][b], blk[a][b]);
+            }
         }
-        A[(size_t)i * KL + l * l + pc] = scale * (double)(s0 - c0);
-        if (m > 0) A[(size_t)i * KL + l * l + pc + 1] = scale * (double)(s1 - c1);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int lr = l0 + rg + 16 * a;
+            if (lr >= nl) continue;
+            const int l = m + lr;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int col = cg + 16 * b, i = i0 + (col >> 1), sn = col & 1;
+                if (i < n_r && (sn == 0 || m > 0))
+                    A[(size_t)i * KL + l * l + pc + sn] = scale * f32_to_f64_alu(s[a][b] - c[a][b]);
+            }
+        }
     }
 }
 
@@ -383,7 +442,8 @@ template <int NT, int CH>
 static void scan_reg_launch(mp_mesh *m, int want_f32)
 {
     launch_pdl(k_scan_reg<NT, CH>, dim3(m->KL), dim3(NT), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
-               m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, m->n_r, m->KL);
+               m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, want_f32 ? m->d_C0 : nullptr, m->n_r,
+               m->KL);
 }
 
 // Shells per thread CH for NT threads per moment column; false when n_r > 16 NT.
@@ -419,7 +479,8 @@ cudaError_t launch_scan(mp_mesh *m, int want_f32)
     if (!done)
         k_scan<kScanThreads><<<m->KL, kScanThreads, 0, m->stream>>>(m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
                                                                     m->d_MR, m->d_MI, m->d_C,
-                                                                    want_f32 ? m->d_C32 : nullptr, m->n_r, m->KL);
+                                                                    want_f32 ? m->d_C32 : nullptr,
+                                                                    want_f32 ? m->d_C0 : nullptr, m->n_r, m->KL);
     prof_end(m, "radial_scan", ev);
     return cudaGetLastError();
 }
@@ -449,8 +510,9 @@ cudaError_t launch_split_theta(mp_mesh *m)
         launch_pdl(k32_theta_pipe, dim3(grid), dim3(threads), smem, m->stream, m->d_F32, m->d_Ith32, m->d_A, m->d_err,
                    m->n_r, m->n_t, L, m->KL, P, ldF, n_items, jsh, tab_bytes, kFourPi * m->G);
     } else {
-        k32_theta_direct<<<m->n_r, 256, 0, m->stream>>>(m->d_F32, m->d_Ith32, m->d_A, m->n_t, L, m->KL, m->T, P, ldF,
-                                                        kFourPi * m->G);
+        const dim3 grid((m->n_r + kMgShells - 1) / kMgShells, L + 1);
+        launch_pdl(k32_theta_mgemm, grid, dim3(256), 0, m->stream, m->d_F32, m->d_Ith32, m->d_A, m->n_r, m->n_t, L,
+                   m->KL, P, ldF, kFourPi * m->G);
     }
     prof_end(m, "split_theta_contract", ev);
     return cudaGetLastError();

@@ -442,8 +442,31 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
 constexpr int kGsS = 2;   // shells per pass
 constexpr int kGsPre = 4; // coefficient registers per thread (kGsS * KL <= kGsPre * threads)
 
+// The m = 0 column is the bulk of Phi and its Legendre sum can cancel: it is formed in
+// double-float arithmetic on the float32 pipe from (hi, lo) pairs of the table T[l] and
+// the coefficients c[l] -- products split exactly by fmaf, the running sum kept as a
+// TwoSum pair -- and leaves as a (hi, lo) pair (relative error near 2^-44).
+__device__ __forceinline__ float2 g0_double_float(const float2 *T, int t_stride, const float2 *c, int L)
+{
+    float s = 0.0f, e = 0.0f;
+    for (int l = 0; l <= L; ++l) {
+        const float2 t = T[(size_t)l * t_stride], k = c[l];
+        const float p = __fmul_rn(t.x, k.x);
+        const float pe = fmaf(t.x, k.x, -p);            // exact error of the leading product
+        const float cross = fmaf(t.x, k.y, __fmul_rn(t.y, k.x));
+        const float s2 = __fadd_rn(s, p);                 // TwoSum of the running sum and p
+        const float bv = __fsub_rn(s2, s);
+        const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bv)), __fsub_rn(p, bv));
+        s = s2;
+        e = __fadd_rn(e, __fadd_rn(se, __fadd_rn(pe, cross)));
+    }
+    const float hi = __fadd_rn(s, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+
 template <int A_TERMS>
 __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict__ C32, const float *__restrict__ Itc,
+                                                         const float2 *__restrict__ C0, const float2 *__restrict__ Itc0,
                                                          uint8_t *__restrict__ Aop, float *__restrict__ G0, int *err,
                                                          int n_r, int n_t, int L, int KL, int Kpad, int ldF,
                                                          uint32_t tab_bytes)
@@ -452,7 +475,9 @@ __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict
     float *sI = reinterpret_cast<float *>(smem_gp);                              // [T][ldF]
     float *sG = reinterpret_cast<float *>(smem_gp + tab_bytes);                  // [kGsS][Kpad][ldF]
     float *sC = sG + (size_t)kGsS * Kpad * ldF;                                  // [kGsS][KL]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sC + (((size_t)kGsS * KL + 1) & ~(size_t)1));
+    float2 *sT0 = reinterpret_cast<float2 *>(sC + (((size_t)kGsS * KL + 1) & ~(size_t)1));  // [L+1][n_t]
+    float2 *sC0 = sT0 + (size_t)(L + 1) * n_t;                                   // [kGsS][L+1]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sC0 + (size_t)kGsS * (L + 1));
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 1);
     const int tid = threadIdx.x, nthr = blockDim.x;
     if (tid == 0) {
@@ -465,10 +490,11 @@ __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict
         mbar_arrive_expect_tx(smem_u32(bar), tab_bytes);
         bulk_load(smem_u32(sI), Itc, tab_bytes, smem_u32(bar));
     }
-    // the table copy overlaps the previous kernel's tail; coefficients only after it completed
+    for (int e = tid; e < (L + 1) * n_t; e += nthr) sT0[e] = Itc0[e];  // static table
+    // the table copies overlap the previous kernel's tail; coefficients only after it completed
     pdl_trigger();
     pdl_wait();
-    const int U = 1 + (L + 1) / 2;      // work units per group of 128 polar cells
+    const int U = (L + 1) / 2;          // work units (order pairs, m >= 1) per group of 128 polar cells
     const int nq = (n_t + 3) / 4;       // float4 units of polar cells
     const int NJ = (nq + 31) / 32;
     const int n_work = kGsS * NJ * U * 32;
@@ -483,6 +509,7 @@ __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict
         sG[((size_t)sh * Kpad + kk) * ldF + e % ldF] = 0.0f;
     }
     float cv[kGsPre];
+    float2 cv0 = make_float2(0.f, 0.f);  // thread e < kGsS (L+1): m = 0 coefficient pair
     auto load_coefficients = [&](int pass) {
 #pragma unroll
         for (int k = 0; k < kGsPre; ++k) {
@@ -491,6 +518,10 @@ __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict
                 const int i = pass * kGsS + e / KL;
                 cv[k] = (i < n_r) ? __ldg(C32 + (size_t)i * KL + e % KL) : 0.0f;
             }
+        }
+        if (tid < kGsS * (L + 1)) {
+            const int i = pass * kGsS + tid / (L + 1);
+            cv0 = (i < n_r) ? C0[(size_t)i * (L + 1) + tid % (L + 1)] : make_float2(0.f, 0.f);
         }
     };
     if ((int)blockIdx.x < n_pass) load_coefficients(blockIdx.x);
@@ -507,7 +538,7 @@ __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict
     auto compute = [&](int pass, int w) {
         const int lane = w & 31;
         int rest = w >> 5;
-        const int u = rest % U;
+        const int u = 1 + rest % U;
         rest /= U;
         const int jg = rest % NJ, sh = rest / NJ;
         const int i = pass * kGsS + sh;
@@ -515,24 +546,6 @@ __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict
         if (i >= n_r || uq >= nq) return;
         const float *cf = sC + (size_t)sh * KL;
         float *gs = sG + (size_t)sh * Kpad * ldF;
-        if (u == 0) {
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float *tr = sI + 4 * uq;
-            for (int l = 0; l <= L; ++l) {
-                const float c = cf[l * l];
-                const float4 t = *reinterpret_cast<const float4 *>(tr);
-                tr += (size_t)(l + 1) * ldF;  // tri(l + 1, 0) = tri(l, 0) + l + 1
-                a.x = fmaf(t.x, c, a.x);
-                a.y = fmaf(t.y, c, a.y);
-                a.z = fmaf(t.z, c, a.z);
-                a.w = fmaf(t.w, c, a.w);
-            }
-            const float av[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj)
-                if (4 * uq + jj < n_t) G0[(size_t)i * n_t + 4 * uq + jj] = av[jj];
-            return;
-        }
         for (int h = 0; h < 2; ++h) {
             const int m = (h == 0) ? u : L + 1 - u;
             if (h == 1 && m <= u) break;  // odd L: the middle order stands alone
@@ -567,8 +580,16 @@ __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict
             const int e = tid + k * nthr;
             if (e < n_cf) sC[e] = cv[k];
         }
+        if (tid < kGsS * (L + 1)) sC0[tid] = cv0;
         __syncthreads();
         for (int w = tid; w < n_work; w += nthr) compute(pass, w);
+        // the m = 0 column in double-float, one cell per thread
+        for (int e = tid; e < kGsS * n_t; e += nthr) {
+            const int sh = e / n_t, j = e - sh * n_t, i = pass * kGsS + sh;
+            if (i < n_r)
+                *reinterpret_cast<float2 *>(G0 + 2 * ((size_t)i * n_t + j)) =
+                    g0_double_float(sT0 + j, n_t, sC0 + (size_t)sh * (L + 1), L);
+        }
         __syncthreads();
         if (pass + (int)gridDim.x < n_pass) load_coefficients(pass + gridDim.x);
         int j = j_first, sg = sg_first;
@@ -612,79 +633,101 @@ __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict
     }
 }
 
+// Theta synthesis for tables that exceed shared memory, one GEMM per order m:
+//   G[i, j][p] = sum_{l = m..L} Itc[tri(l,m)][j] C32[i][l^2 + p],   p in {pc, ps},
+// M = polar cells, N = shells (cos and sin together), K = degrees.  Block (64 polar
+// cells, 32 shells, m) stages the table rows and the coefficients of K chunks of 32
+// degrees in shared memory; thread (rg, cg) owns cells cg + 16 a (a < 4) and shells
+// rg + 16 b (b < 2), cos and sin.  The results leave as the bf16 terms of the canonical
+// MMA layout ((cos, sin) pairs, 4 bytes per term) or, for m = 0, the float32 column G0;
+// K columns past 2L keep the zeros the buffer was created with.
+constexpr int kGmCells = 64, kGmShells = 32, kGmK = 32;
+
 template <int A_TERMS>
-__global__ void __launch_bounds__(256) k_gsynth(const float *__restrict__ C32, const float *__restrict__ Itc,
-                                                uint8_t *__restrict__ Aop, float *__restrict__ G0, int n_t, int L,
-                                                int KL, int Kpad, int ldF)
+__global__ void __launch_bounds__(256) k_gsynth_mgemm(const float *__restrict__ C32, const float *__restrict__ Itc,
+                                                      const float2 *__restrict__ C0, const float2 *__restrict__ Itc0,
+                                                      uint8_t *__restrict__ Aop, float *__restrict__ G0, int n_r,
+                                                      int n_t, int L, int KL, int Kpad, int ldF)
 {
-    // block (i, y): shell i, polar cells j = y * jpb + threadIdx.y; threadIdx.x = group gi of
-    // eight K columns (p = 8 gi + 1 .. 8 gi + 8), and one extra lane group for p = 0
-    extern __shared__ float sCrow[];  // [KL]
-    const int i = blockIdx.x;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int e = tid; e < KL; e += blockDim.x * blockDim.y) sCrow[e] = C32[(size_t)i * KL + e];
-    __syncthreads();
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (j >= n_t) return;
-    const long long row = (long long)i * n_t + j;
-    const float *itab = Itc + j;
-    const int ngrp = Kpad / 8;
-    const int gi = threadIdx.x;
-    if (gi == ngrp) {
-        float g0 = 0.0f, g1 = 0.0f;
-        int l = 0;
-        for (; l + 1 <= L; l += 2) {
-            g0 = fmaf(__ldg(itab + (size_t)tri(l, 0) * ldF), sCrow[l * l], g0);
-            g1 = fmaf(__ldg(itab + (size_t)tri(l + 1, 0) * ldF), sCrow[(l + 1) * (l + 1)], g1);
+    __shared__ __align__(16) float sT[kGmK][kGmCells + 4];
+    __shared__ float sC[kGmK][2 * kGmShells + 1];
+    pdl_wait();  // C32 comes from the previous kernel
+    const int j0 = blockIdx.x * kGmCells, i0 = blockIdx.y * kGmShells, m = blockIdx.z;
+    if (m == 0) {
+        // the m = 0 column in double-float (block-uniform branch)
+        for (int e = threadIdx.x; e < kGmCells * kGmShells; e += blockDim.x) {
+            const int j = j0 + e % kGmCells, i = i0 + e / kGmCells;
+            if (j < n_t && i < n_r)
+                *reinterpret_cast<float2 *>(G0 + 2 * ((size_t)i * n_t + j)) =
+                    g0_double_float(Itc0 + j, n_t, C0 + (size_t)i * (L + 1), L);
         }
-        if (l <= L) g0 = fmaf(__ldg(itab + (size_t)tri(l, 0) * ldF), sCrow[l * l], g0);
-        G0[row] = g0 + g1;
         return;
     }
-    if (gi > ngrp) return;
-    float gv[8];
+    const int nl = L + 1 - m;
+    const int pc = (m == 0) ? 0 : 2 * m - 1;
+    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+    float gc[4][2], gs[4][2];
 #pragma unroll
-    for (int mm = 0; mm < 4; ++mm) {
-        const int m = 4 * gi + mm + 1;
-        float ac = 0.0f, as = 0.0f, bc = 0.0f, bs = 0.0f;
-        if (m <= L) {
-            const float *cc = sCrow + 2 * m - 1;  // C[i][l^2 + 2m - 1], C[i][l^2 + 2m]
-            int l = m;
-            for (; l + 1 <= L; l += 2) {
-                const float w0 = __ldg(itab + (size_t)tri(l, m) * ldF);
-                const float w1 = __ldg(itab + (size_t)tri(l + 1, m) * ldF);
-                ac = fmaf(w0, cc[l * l], ac);
-                as = fmaf(w0, cc[l * l + 1], as);
-                bc = fmaf(w1, cc[(l + 1) * (l + 1)], bc);
-                bs = fmaf(w1, cc[(l + 1) * (l + 1) + 1], bs);
-            }
-            if (l <= L) {
-                const float w0 = __ldg(itab + (size_t)tri(l, m) * ldF);
-                ac = fmaf(w0, cc[l * l], ac);
-                as = fmaf(w0, cc[l * l + 1], as);
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) gc[a][b] = gs[a][b] = 0.0f;
+    for (int l0 = 0; l0 < nl; l0 += kGmK) {
+        __syncthreads();
+        for (int e = tid; e < kGmK * (kGmCells / 4); e += blockDim.x) {
+            const int r = e >> 4, q = e & 15, j = j0 + 4 * q;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (l0 + r < nl && j < ldF) v = *reinterpret_cast<const float4 *>(Itc + (size_t)tri(m + l0 + r, m) * ldF + j);
+            *reinterpret_cast<float4 *>(&sT[r][4 * q]) = v;
+        }
+        for (int e = tid; e < kGmK * 2 * kGmShells; e += blockDim.x) {
+            const int r = e / (2 * kGmShells), col = e % (2 * kGmShells);
+            const int i = i0 + (col >> 1), sn = col & 1, l = m + l0 + r;
+            float v = 0.0f;
+            if (l0 + r < nl && i < n_r && (sn == 0 || m > 0)) v = __ldg(C32 + (size_t)i * KL + l * l + pc + sn);
+            sC[r][col] = v;
+        }
+        __syncthreads();
+        const int kn = min(kGmK, nl - l0);
+        for (int r = 0; r < kn; ++r) {
+            float t[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) t[a] = sT[r][cg + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const float cc = sC[r][2 * (rg + 16 * b)], cs = sC[r][2 * (rg + 16 * b) + 1];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    gc[a][b] = fmaf(t[a], cc, gc[a][b]);
+                    gs[a][b] = fmaf(t[a], cs, gs[a][b]);
+                }
             }
         }
-        gv[2 * mm] = ac + bc;
-        gv[2 * mm + 1] = as + bs;
-    }
-    uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const float x0 = gv[2 * c], x1 = gv[2 * c + 1];
-        const uint32_t t0 = pack_bf16x2(x0, x1);
-        const float r0 = x0 - bf16lo_to_f32(t0), r1 = x1 - bf16hi_to_f32(t0);
-        const uint32_t t1 = pack_bf16x2(r0, r1);
-        w0[c] = t0;
-        w1[c] = t1;
-        if (A_TERMS == 3) w2[c] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
     }
     const size_t a_term_bytes = (size_t)128 * Kpad * 2;
-    const int r = (int)(row & 127);
-    uint8_t *dst = Aop + (size_t)(row >> 7) * A_TERMS * a_term_bytes + (size_t)(r >> 3) * (Kpad * 16) + (r & 7) * 16 +
-                   gi * 128;
-    *reinterpret_cast<uint4 *>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-    *reinterpret_cast<uint4 *>(dst + a_term_bytes) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-    if (A_TERMS == 3) *reinterpret_cast<uint4 *>(dst + 2 * a_term_bytes) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int i = i0 + rg + 16 * b;
+        if (i >= n_r) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int j = j0 + cg + 16 * a;
+            if (j >= n_t) continue;
+            const long long row = (long long)i * n_t + j;
+            const int k = 2 * m - 2;  // K column of the cos term; the sin term follows
+            const int r = (int)(row & 127);
+            uint8_t *dst = Aop + (size_t)(row >> 7) * A_TERMS * a_term_bytes + (size_t)(r >> 3) * (Kpad * 16) +
+                           (size_t)(k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+            const float x0 = gc[a][b], x1 = gs[a][b];
+            const uint32_t t0 = pack_bf16x2(x0, x1);
+            const float r0 = x0 - bf16lo_to_f32(t0), r1 = x1 - bf16hi_to_f32(t0);
+            const uint32_t t1 = pack_bf16x2(r0, r1);
+            *reinterpret_cast<uint32_t *>(dst) = t0;
+            *reinterpret_cast<uint32_t *>(dst + a_term_bytes) = t1;
+            if (A_TERMS == 3)
+                *reinterpret_cast<uint32_t *>(dst + 2 * a_term_bytes) =
+                    pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -727,7 +770,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
     const int nkk = Kpad / 16;
     const int n_chunks = prm.n_nc * nkk;
     const int b_slots = prm.b_resident ? n_chunks : NS_B;
-    const uint32_t a_stage = prm.a_bytes + 512;  // A operand terms + the tile's 128 m = 0 values
+    const uint32_t a_stage = prm.a_bytes + 1024;  // A operand terms + the tile's 128 m = 0 (hi, lo) pairs
     uint8_t *stg = smem;                                           // [16 warps][NSTG][4096]
     uint8_t *sA = stg + (size_t)EPI_WARPS * NSTG * STG_BYTES;      // [NS_A][a_stage]
     uint8_t *sB = sA + (size_t)NS_A * a_stage;                     // [b_slots][bchunk]
@@ -792,7 +835,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                 uint8_t *dst = sA + (size_t)ra.idx * a_stage;
                 mbar_arrive_expect_tx(fb, a_stage);
                 bulk_load(smem_u32(dst), prm.Aop + (size_t)tile * prm.a_bytes, prm.a_bytes, fb);
-                bulk_load(smem_u32(dst + prm.a_bytes), prm.G0 + (size_t)tile * 128, 512, fb);
+                bulk_load(smem_u32(dst + prm.a_bytes), prm.G0 + (size_t)tile * 256, 1024, fb);
                 if (!prm.b_resident) {
                     for (int c = 0; c < n_chunks && ok; ++c, rb.next(NS_B)) {
                         ok = mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err);
@@ -878,7 +921,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
         for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ra.next(NS_A)) {
             ok = warp_all(mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err));
             if (!ok) break;
-            const float g0 = reinterpret_cast<const float *>(sA + (size_t)ra.idx * a_stage + prm.a_bytes)[row];
+            const float2 g0 = reinterpret_cast<const float2 *>(sA + (size_t)ra.idx * a_stage + prm.a_bytes)[row];
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&a_empty[ra.idx]));
             const long long box_row = (long long)tile * kBM + qd * 32;
@@ -890,17 +933,11 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                 tc_fence_after();
                 const uint32_t tcol = tmem_base + lane_base + (uint32_t)buf * acc_stride;
                 const int nmine = (NC / 16 - quarter + 3) / 4;  // chunks quarter, quarter + 4, ...
-                // the next chunk's accumulators are requested before this chunk is converted
-                uint32_t vn[16];
-                if (nmine > 0) tmem_ld16(tcol + (uint32_t)((quarter + 4 * rotated_chunk(0, tile, nmine)) * 16), vn);
                 for (int it = 0; it < nmine; ++it) {
                     const int ch = quarter + 4 * rotated_chunk(it, tile, nmine);
                     uint32_t v[16];
+                    tmem_ld16(tcol + (uint32_t)(ch * 16), v);
                     tmem_ld_wait();
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) v[e] = vn[e];
-                    if (it + 1 < nmine)
-                        tmem_ld16(tcol + (uint32_t)((quarter + 4 * rotated_chunk(it + 1, tile, nmine)) * 16), vn);
                     uint8_t *st = stg + (size_t)(cw * NSTG + (cs % NSTG)) * STG_BYTES;
                     ++cs;
                     if (lane == 0) {
@@ -914,8 +951,9 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         uint32_t lo0, hi0, lo1, hi1;
-                        f32_to_f64w_finite(__uint_as_float(v[2 * e]) + g0, lo0, hi0);
-                        f32_to_f64w_finite(__uint_as_float(v[2 * e + 1]) + g0, lo1, hi1);
+                        // Phi = m >= 1 part + m = 0 column (low part first: one rounding of the sum)
+                        f32_to_f64w_finite((__uint_as_float(v[2 * e]) + g0.y) + g0.x, lo0, hi0);
+                        f32_to_f64w_finite((__uint_as_float(v[2 * e + 1]) + g0.y) + g0.x, lo1, hi1);
                         *reinterpret_cast<uint4 *>(srow + ((e ^ (lane & 7)) << 4)) = make_uint4(lo0, hi0, lo1, hi1);
                     }
                     fence_proxy_async_smem();
@@ -1030,6 +1068,16 @@ __global__ void k_tab_theta32(const double *__restrict__ Ith, const double *__re
 
 constexpr int kSmemLimit = 232448;  // 227 KB opt-in per block on sm_100-class parts
 
+// theta table of the m = 0 column as (hi, lo) float pairs: Itc0[l][j] = Ith[tri(l,0)][j] / dmu_j
+__global__ void k_tab_theta0(const double *__restrict__ Ith, const double *__restrict__ dmu, int n_t, int L,
+                             float2 *__restrict__ Itc0)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (L + 1) * n_t) return;
+    const int l = idx / n_t, j = idx % n_t;
+    Itc0[idx] = f32_pair(Ith[(size_t)tri(l, 0) * n_t + j] / dmu[j]);
+}
+
 template <int A_TERMS, int NPROD>
 cudaError_t set_smem_attrs()
 {
@@ -1057,7 +1105,7 @@ int proj_smem_bytes(const SplitPlan &pl, int ns_s, int ns_o, int b_resident)
 int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs)
 {
     const int bchunk = 3 * pl.NC * 32;
-    const int a_stage = pl.a_terms * kBM * pl.Kpad * 2 + 512;
+    const int a_stage = pl.a_terms * kBM * pl.Kpad * 2 + 1024;
     return 1024 + synth::EPI_WARPS * stg_bufs * synth::STG_BYTES + ns_a * a_stage + b_slots * bchunk + 512;
 }
 
@@ -1126,6 +1174,8 @@ cudaError_t launch_split_tables(mp_mesh *m)
         const long long n = (long long)m->T * m->n_t;
         k_tab_theta32<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(m->d_Ith, m->d_dmu, m->n_t, m->T, pl.ldF,
                                                                           m->d_Ith32, m->d_Itc32);
+        const int n0 = (m->L + 1) * m->n_t;
+        k_tab_theta0<<<(n0 + 255) / 256, 256, 0, m->stream>>>(m->d_Ith, m->d_dmu, m->n_t, m->L, m->d_Itc0);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1176,13 +1226,13 @@ cudaError_t launch_split_synth(mp_mesh *m, double *phi)
     const int n_tiles = (int)((m->R + kBM - 1) / kBM);
     cudaEvent_t ev;
     prof_begin(m, "split_theta_synth", &ev);
-    const int ngrp = pl.Kpad / 8 + 1;  // K groups plus the m = 0 column
     const uint32_t tab_bytes = (uint32_t)((size_t)m->T * pl.ldF * 4);
-    const int U = 1 + (m->L + 1) / 2, NJ = ((m->n_t + 3) / 4 + 31) / 32;
-    const int pipe_threads = std::min(1024, kGsS * NJ * U * 32);
+    const int U = (m->L + 1) / 2, NJ = ((m->n_t + 3) / 4 + 31) / 32;
+    const int pipe_threads = std::max(64, std::min(1024, kGsS * NJ * U * 32));
     const size_t pipe_smem = (size_t)tab_bytes + (size_t)kGsS * pl.Kpad * pl.ldF * 4 +
-                             (((size_t)kGsS * m->KL + 1) & ~(size_t)1) * 4 + 16;
-    if (pipe_smem <= 200 * 1024 && kGsS * m->KL <= kGsPre * pipe_threads) {
+                             (((size_t)kGsS * m->KL + 1) & ~(size_t)1) * 4 +
+                             ((size_t)(m->L + 1) * m->n_t + (size_t)kGsS * (m->L + 1)) * 8 + 16;
+    if (pipe_smem <= 200 * 1024 && kGsS * m->KL <= kGsPre * pipe_threads && kGsS * (m->L + 1) <= pipe_threads) {
         static bool attr_set = false;
         if (!attr_set) {
             cudaFuncSetAttribute(k_gsynth_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1192,25 +1242,22 @@ cudaError_t launch_split_synth(mp_mesh *m, double *phi)
         const int grid = std::min((m->n_r + kGsS - 1) / kGsS, m->num_sms);
         if (pl.a_terms == 2)
             launch_pdl(k_gsynth_pipe<2>, dim3(grid), dim3(pipe_threads), pipe_smem, m->stream, m->d_C32, m->d_Itc32,
-                       m->d_Aop, m->d_G0, m->d_err, m->n_r, m->n_t, m->L, m->KL, pl.Kpad, pl.ldF, tab_bytes);
+                       m->d_C0, m->d_Itc0, m->d_Aop, m->d_G0, m->d_err, m->n_r, m->n_t, m->L, m->KL, pl.Kpad,
+                       pl.ldF, tab_bytes);
         else
             launch_pdl(k_gsynth_pipe<3>, dim3(grid), dim3(pipe_threads), pipe_smem, m->stream, m->d_C32, m->d_Itc32,
-                       m->d_Aop, m->d_G0, m->d_err, m->n_r, m->n_t, m->L, m->KL, pl.Kpad, pl.ldF, tab_bytes);
+                       m->d_C0, m->d_Itc0, m->d_Aop, m->d_G0, m->d_err, m->n_r, m->n_t, m->L, m->KL, pl.Kpad,
+                       pl.ldF, tab_bytes);
     } else {
-        const int jpb = std::max(1, std::min(m->n_t, 256 / ngrp));
-        const dim3 block(ngrp, jpb);
-        const dim3 grid(m->n_r, (m->n_t + jpb - 1) / jpb);
-        const size_t smem = (size_t)m->KL * sizeof(float);
-        if (smem > 48 * 1024) {
-            cudaFuncSetAttribute(k_gsynth<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(k_gsynth<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        }
+        const dim3 grid((m->n_t + kGmCells - 1) / kGmCells, (m->n_r + kGmShells - 1) / kGmShells, m->L + 1);
         if (pl.a_terms == 2)
-            k_gsynth<2><<<grid, block, smem, m->stream>>>(m->d_C32, m->d_Itc32, m->d_Aop, m->d_G0, m->n_t, m->L,
-                                                          m->KL, pl.Kpad, pl.ldF);
+            launch_pdl(k_gsynth_mgemm<2>, grid, dim3(256), 0, m->stream, m->d_C32, m->d_Itc32, m->d_C0, m->d_Itc0,
+                       m->d_Aop, m->d_G0,
+                       m->n_r, m->n_t, m->L, m->KL, pl.Kpad, pl.ldF);
         else
-            k_gsynth<3><<<grid, block, smem, m->stream>>>(m->d_C32, m->d_Itc32, m->d_Aop, m->d_G0, m->n_t, m->L,
-                                                          m->KL, pl.Kpad, pl.ldF);
+            launch_pdl(k_gsynth_mgemm<3>, grid, dim3(256), 0, m->stream, m->d_C32, m->d_Itc32, m->d_C0, m->d_Itc0,
+                       m->d_Aop, m->d_G0,
+                       m->n_r, m->n_t, m->L, m->KL, pl.Kpad, pl.ldF);
     }
     prof_end(m, "split_theta_synth", ev);
     SynthParams prm;

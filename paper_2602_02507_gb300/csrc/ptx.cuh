@@ -332,6 +332,13 @@ __device__ __forceinline__ double f32_to_f64_alu(float x)
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// float64 -> (hi, lo) float pair with hi + lo = x to about 2^-48 relative.
+__device__ __forceinline__ float2 f32_pair(double x)
+{
+    const float hi = f64_to_f32_alu(x);
+    return make_float2(hi, f64_to_f32_alu(x - f32_to_f64_alu(hi)));
+}
+
 // Round-to-nearest bf16 pair packed in one word (x in the low half).
 __device__ __forceinline__ uint32_t pack_bf16x2(float x, float y)
 {
