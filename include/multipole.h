@@ -95,6 +95,8 @@ typedef struct {
     double r_ref;            /* reference radius of the radial kernel scaling        */
     double G;                /* gravitational constant, S = 4 pi G rho               */
     size_t device_bytes;     /* device memory the mesh holds (tables + workspace)    */
+    int tuned_candidates;    /* configurations the last mp_autotune timed (0: none,  */
+                             /* or the choice came from the cache file)              */
 } mp_mesh_info;
 
 /*

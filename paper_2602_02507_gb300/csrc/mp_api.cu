@@ -498,6 +498,7 @@ mp_status mp_mesh_get_info(const mp_mesh *m, mp_mesh_info *info)
     info->r_ref = m->r_ref;
     info->G = m->G;
     info->device_bytes = m->device_bytes;
+    info->tuned_candidates = m->tuned_candidates;
     return MP_OK;
 }
 
@@ -785,6 +786,7 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
                     m->plan.ns_b = ns_b;
                     m->plan.scan_threads = sw;
                     m->plan.proj_b_resident = br ? m->plan.proj_res_ok : !m->plan.proj_ring_ok;
+                    m->tuned_candidates = 0;
                     drop_graph(m);
                     return MP_OK;
                 }
@@ -806,8 +808,10 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     if (m->eff_prec == MP_PREC_FP64) {
         for (int sw : sws) cands.push_back({base.ns_s, base.ns_b, sw, 0});
     } else {
+        // the synthesis table ring depth only matters when the table is not resident
+        const int ns_b_lo = base.b_resident ? base.ns_b : 2;
         for (int ns_s = 3; ns_s <= base.ns_s; ++ns_s)
-            for (int ns_b = 2; ns_b <= base.ns_b; ++ns_b)
+            for (int ns_b = ns_b_lo; ns_b <= base.ns_b; ++ns_b)
                 for (int br = 0; br <= 1; ++br)
                     if (br ? base.proj_res_ok : base.proj_ring_ok)
                         for (int sw : sws) cands.push_back({ns_s, ns_b, sw, br});
@@ -851,6 +855,7 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     m->plan.ns_b = best_c.ns_b;
     m->plan.scan_threads = best_c.sw;
     m->plan.proj_b_resident = best_c.br;
+    m->tuned_candidates = (int)cands.size();
     drop_graph(m);
     if (st != MP_OK) {
         m->plan = base;

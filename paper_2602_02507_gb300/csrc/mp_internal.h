@@ -119,6 +119,7 @@ struct mp_mesh {
 
     // profiling
     int profiling = 0;
+    int tuned_candidates = 0;  // configurations the last mp_autotune timed
     std::vector<std::pair<const char *, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
     std::map<std::string, mp::ProfileEntry> prof;
     std::vector<cudaEvent_t> event_pool;

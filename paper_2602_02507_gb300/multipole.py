@@ -36,7 +36,7 @@ class MeshInfo(ctypes.Structure):
     _fields_ = [("n_r", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
                 ("l_max", ctypes.c_int), ("n_moments", ctypes.c_int), ("precision", ctypes.c_int),
                 ("effective_precision", ctypes.c_int), ("r_ref", ctypes.c_double), ("G", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("tuned_candidates", ctypes.c_int)]
 
 
 def load_library(path: str = LIB_PATH):

@@ -155,6 +155,7 @@ def test_autotune_keeps_results(tmp_path):
         mesh.set_density(rho)
         mesh.set_phi_output(phi)
         mesh.autotune(cache)
+        assert mesh.info()["tuned_candidates"] > 1  # configurations were actually timed
         mesh.solve()
         mesh.synchronize()
         assert phi_rel_err(phi.cpu().numpy(), ref) <= 1e-6
@@ -162,3 +163,4 @@ def test_autotune_keeps_results(tmp_path):
     with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3") as mesh2:
         mesh2.set_density(rho)
         mesh2.autotune(cache)  # served from the cache
+        assert mesh2.info()["tuned_candidates"] == 0
