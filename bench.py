@@ -48,7 +48,7 @@ SPLIT_PRECISION = "bf16x3"
 #               source file of the kernel, sha1 of that file and the shared headers at
 #               capture time); an entry whose sources changed since is ignored
 NCU_TRAFFIC = {
-    "split_phi_project_tc": (134315264 + 3236608, "mp_split.cu", "e6f4d129ff6d0cce1abdf0afe4dce45cd55b4ffc"),
+    "split_phi_project_tc": (134324992 + 2874880, "mp_split.cu", "7e30c44511d95b17c87d7dadf3f0b3c0a40f60da"),
 }
 KERNEL_HEADERS = ("ptx.cuh", "mp_internal.h", "mp_errors.h")
 
