@@ -177,6 +177,17 @@ MP_API mp_status mp_get_moments(mp_mesh *mesh, double *ang_dev, double *mr_dev, 
  */
 MP_API mp_status mp_solve_host(mp_mesh *mesh, const double *rho_host, double *phi_host);
 
+/*
+ * The same round trip without waiting: the upload, the solve and the download
+ * are enqueued and the call returns.  The mesh keeps two device staging pairs
+ * and uses them in turn, with the uploads and downloads on streams of its own,
+ * so that the download of one call overlaps the upload of the next.  rho_host
+ * must stay unchanged and phi_host unread until mp_mesh_synchronize() (which
+ * also reports device-side errors); both should be pinned for the copies to run
+ * asynchronously.  mp_get_phi() then returns the last call's Phi.
+ */
+MP_API mp_status mp_solve_host_async(mp_mesh *mesh, const double *rho_host, double *phi_host);
+
 /* Wait for the mesh's stream and return (then clear) any device-side error. */
 MP_API mp_status mp_mesh_synchronize(mp_mesh *mesh);
 

@@ -155,7 +155,8 @@ static void free_mesh_buffers(mp_mesh *m)
     void *ptrs[] = {m->d_r,   m->d_Ith,  m->d_dmu,    m->d_Iph,   m->d_Iphc,   m->d_WR,    m->d_WI,
                     m->d_GR,  m->d_GI,   m->d_V,      m->d_A,     m->d_MR,     m->d_MI,    m->d_C,
                     m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_Ith32, m->d_Itc32, m->d_Itc0, m->d_C0, m->d_colsum,
-                    m->d_tabB, m->d_tabT, m->d_Aop, m->d_G0, m->phi_own, m->rho_stage, m->d_err};
+                    m->d_tabB, m->d_tabT, m->d_Aop, m->d_G0, m->phi_own, m->h_rho[0], m->h_rho[1],
+                    m->h_phi[0], m->h_phi[1], m->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &pe : m->prof_pending) {
@@ -182,11 +183,11 @@ struct DeviceGuard {
 
 static void drop_graph(mp_mesh *m)
 {
-    if (m->g_exec) cudaGraphExecDestroy(m->g_exec);
-    if (m->g_graph) cudaGraphDestroy(m->g_graph);
-    m->g_exec = nullptr;
-    m->g_graph = nullptr;
-    m->g_rho = m->g_phi = nullptr;
+    for (auto &g : m->g_slots) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g = mp_mesh::GraphSlot();
+    }
 }
 
 static mp_status ensure_phi_own(mp_mesh *m)
@@ -223,13 +224,22 @@ static mp_status run_solve(mp_mesh *m, const double *rho, double *phi)
 }
 
 // The solve's kernel chain replayed as one CUDA graph launch on the mesh stream.
-// The graph is captured on a private stream (the caller's stream may be the
-// legacy default stream, which cannot be captured) and captured again when the
-// bound density or potential buffer changes.
+// A graph is captured on a private stream (the caller's stream may be the legacy
+// default stream, which cannot be captured) per (density, potential) binding; a
+// few bindings stay cached (the host round trips alternate two), the least
+// recently used one is captured over.
 static mp_status solve_graph(mp_mesh *m, const double *rho, double *phi)
 {
-    if (!m->g_exec || m->g_rho != rho || m->g_phi != phi) {
-        drop_graph(m);
+    mp_mesh::GraphSlot *slot = nullptr;
+    for (auto &g : m->g_slots)
+        if (g.exec && g.rho == rho && g.phi == phi) slot = &g;
+    if (!slot) {
+        slot = &m->g_slots[0];
+        for (auto &g : m->g_slots)
+            if (!g.exec || g.used < slot->used) slot = &g;
+        if (slot->exec) cudaGraphExecDestroy(slot->exec);
+        if (slot->graph) cudaGraphDestroy(slot->graph);
+        *slot = mp_mesh::GraphSlot();
         if (!m->g_cap) MP_TRY(cudaStreamCreateWithFlags(&m->g_cap, cudaStreamNonBlocking));
         cudaStream_t saved = m->stream;
         m->stream = m->g_cap;
@@ -247,16 +257,18 @@ static mp_status solve_graph(mp_mesh *m, const double *rho, double *phi)
             return st;
         }
         if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&m->g_exec, g, 0);
+        e = cudaGraphInstantiate(&slot->exec, g, 0);
         if (e != cudaSuccess) {
             cudaGraphDestroy(g);
+            slot->exec = nullptr;
             return cuda_status(e, "cudaGraphInstantiate");
         }
-        m->g_graph = g;
-        m->g_rho = rho;
-        m->g_phi = phi;
+        slot->graph = g;
+        slot->rho = rho;
+        slot->phi = phi;
     }
-    MP_TRY(cudaGraphLaunch(m->g_exec, m->stream));
+    slot->used = ++m->g_clock;
+    MP_TRY(cudaGraphLaunch(slot->exec, m->stream));
     return MP_OK;
 }
 
@@ -468,8 +480,17 @@ mp_status mp_mesh_destroy(mp_mesh *m)
     if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
     DeviceGuard dg(m->device);
     cudaStreamSynchronize(m->stream);
+    if (m->h_up) cudaStreamSynchronize(m->h_up);
+    if (m->h_down) cudaStreamSynchronize(m->h_down);
     drop_graph(m);
     if (m->g_cap) cudaStreamDestroy(m->g_cap);
+    for (int b = 0; b < 2; ++b) {
+        if (m->h_uploaded[b]) cudaEventDestroy(m->h_uploaded[b]);
+        if (m->h_solved[b]) cudaEventDestroy(m->h_solved[b]);
+        if (m->h_downloaded[b]) cudaEventDestroy(m->h_downloaded[b]);
+    }
+    if (m->h_up) cudaStreamDestroy(m->h_up);
+    if (m->h_down) cudaStreamDestroy(m->h_down);
     free_mesh_buffers(m);
     delete m;
     return MP_OK;
@@ -527,6 +548,7 @@ mp_status mp_solve(mp_mesh *m)
         if (st != MP_OK) return st;
         phi = m->phi_own;
     }
+    m->last_phi = phi;
     // per-kernel timing needs events between the kernels: launch them one by one
     if (m->profiling) return run_solve(m, m->rho, phi);
     return solve_graph(m, m->rho, phi);
@@ -536,7 +558,7 @@ mp_status mp_get_phi(mp_mesh *m, double *phi_dev)
 {
     if (!m || !phi_dev) return set_error(MP_ERR_INVALID_ARG, "NULL argument");
     if (!m->solved) return set_error(MP_ERR_NOT_READY, "no solve has run");
-    const double *src = m->phi_user ? m->phi_user : m->phi_own;
+    const double *src = m->last_phi;
     if (src == phi_dev) return MP_OK;
     DeviceGuard dg(m->device);
     MP_TRY(cudaMemcpyAsync(phi_dev, src, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
@@ -560,6 +582,8 @@ mp_status mp_mesh_synchronize(mp_mesh *m)
     if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
     DeviceGuard dg(m->device);
     MP_TRY(cudaStreamSynchronize(m->stream));
+    if (m->h_up) MP_TRY(cudaStreamSynchronize(m->h_up));
+    if (m->h_down) MP_TRY(cudaStreamSynchronize(m->h_down));
     int err = 0;
     MP_TRY(cudaMemcpy(&err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
@@ -571,21 +595,49 @@ mp_status mp_mesh_synchronize(mp_mesh *m)
     return MP_OK;
 }
 
-mp_status mp_solve_host(mp_mesh *m, const double *rho_host, double *phi_host)
+mp_status mp_solve_host_async(mp_mesh *m, const double *rho_host, double *phi_host)
 {
     if (!m || !rho_host || !phi_host) return set_error(MP_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard dg(m->device);
-    if (!m->rho_stage) {
-        mp_status st = dalloc(m, &m->rho_stage, (size_t)m->N);
-        if (st != MP_OK) return st;
+    if (!m->h_up) {
+        MP_TRY(cudaStreamCreateWithFlags(&m->h_up, cudaStreamNonBlocking));
+        MP_TRY(cudaStreamCreateWithFlags(&m->h_down, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            MP_TRY(cudaEventCreateWithFlags(&m->h_uploaded[b], cudaEventDisableTiming));
+            MP_TRY(cudaEventCreateWithFlags(&m->h_solved[b], cudaEventDisableTiming));
+            MP_TRY(cudaEventCreateWithFlags(&m->h_downloaded[b], cudaEventDisableTiming));
+        }
     }
-    mp_status st = ensure_phi_own(m);
-    if (st != MP_OK) return st;
+    const int b = m->h_slot;
+    for (double **buf : {&m->h_rho[b], &m->h_phi[b]})
+        if (!*buf) {
+            mp_status st = dalloc(m, buf, (size_t)m->N);
+            if (st != MP_OK) return st;
+        }
     const size_t bytes = (size_t)m->N * sizeof(double);
-    MP_TRY(cudaMemcpyAsync(m->rho_stage, rho_host, bytes, cudaMemcpyHostToDevice, m->stream));
-    st = m->profiling ? run_solve(m, m->rho_stage, m->phi_own) : solve_graph(m, m->rho_stage, m->phi_own);
+    // upload into staging pair b once the solve that last read it has run
+    MP_TRY(cudaStreamWaitEvent(m->h_up, m->h_solved[b], 0));
+    MP_TRY(cudaMemcpyAsync(m->h_rho[b], rho_host, bytes, cudaMemcpyHostToDevice, m->h_up));
+    MP_TRY(cudaEventRecord(m->h_uploaded[b], m->h_up));
+    // solve on the mesh stream once the upload landed and the last download of pair b left
+    MP_TRY(cudaStreamWaitEvent(m->stream, m->h_uploaded[b], 0));
+    MP_TRY(cudaStreamWaitEvent(m->stream, m->h_downloaded[b], 0));
+    mp_status st = m->profiling ? run_solve(m, m->h_rho[b], m->h_phi[b]) : solve_graph(m, m->h_rho[b], m->h_phi[b]);
     if (st != MP_OK) return st;
-    MP_TRY(cudaMemcpyAsync(phi_host, m->phi_own, bytes, cudaMemcpyDeviceToHost, m->stream));
+    m->last_phi = m->h_phi[b];
+    MP_TRY(cudaEventRecord(m->h_solved[b], m->stream));
+    // download on its own stream: it overlaps the next call's upload
+    MP_TRY(cudaStreamWaitEvent(m->h_down, m->h_solved[b], 0));
+    MP_TRY(cudaMemcpyAsync(phi_host, m->h_phi[b], bytes, cudaMemcpyDeviceToHost, m->h_down));
+    MP_TRY(cudaEventRecord(m->h_downloaded[b], m->h_down));
+    m->h_slot = b ^ 1;
+    return MP_OK;
+}
+
+mp_status mp_solve_host(mp_mesh *m, const double *rho_host, double *phi_host)
+{
+    mp_status st = mp_solve_host_async(m, rho_host, phi_host);
+    if (st != MP_OK) return st;
     return mp_mesh_synchronize(m);
 }
 
@@ -714,6 +766,7 @@ mp_status mp_batch_solve(mp_batch *b)
             return cuda_status(e, "cudaStreamBeginCapture");
         }
         for (mp_mesh *m : b->meshes) {
+            m->last_phi = m->phi_user ? m->phi_user : m->phi_own;
             st = run_solve(m, m->rho, m->phi_user ? m->phi_user : m->phi_own);
             if (st != MP_OK) break;
         }

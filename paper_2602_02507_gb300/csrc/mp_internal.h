@@ -104,18 +104,32 @@ struct mp_mesh {
     const double *rho = nullptr;
     double *phi_user = nullptr;
     double *phi_own = nullptr;
-    double *rho_stage = nullptr;  // device copy target of mp_solve_host
+    // host round trips (mp_solve_host, mp_solve_host_async): two device staging pairs used
+    // in turn, uploads and downloads on streams of their own, events for buffer reuse
+    double *h_rho[2] = {nullptr, nullptr}, *h_phi[2] = {nullptr, nullptr};
+    cudaStream_t h_up = nullptr, h_down = nullptr;
+    cudaEvent_t h_uploaded[2] = {nullptr, nullptr}, h_solved[2] = {nullptr, nullptr};
+    cudaEvent_t h_downloaded[2] = {nullptr, nullptr};
+    int h_slot = 0;
+    const double *last_phi = nullptr;  // device buffer holding the last solve's Phi
     int *d_err = nullptr;
     int solved = 0;
 
     // TMA descriptors, cached per bound pointer
     CUtensorMap tm_rho{}, tm_phi{};
     const void *tm_rho_ptr = nullptr, *tm_phi_ptr = nullptr;
-    // the solve's kernel chain as one CUDA graph (captured on g_cap for the bound buffers)
+    // the solve's kernel chain as CUDA graphs, one per (density, potential) binding in use
+    // (captured on g_cap), least recently used replaced
+    struct GraphSlot {
+        const void *rho = nullptr, *phi = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long used = 0;
+    };
+    static constexpr int kGraphSlots = 4;
+    GraphSlot g_slots[kGraphSlots];
+    unsigned long long g_clock = 0;
     cudaStream_t g_cap = nullptr;
-    cudaGraph_t g_graph = nullptr;
-    cudaGraphExec_t g_exec = nullptr;
-    const void *g_rho = nullptr, *g_phi = nullptr;
 
     // profiling
     int profiling = 0;

@@ -60,6 +60,7 @@ def load_library(path: str = LIB_PATH):
         "mp_get_phi": [vp, vp],
         "mp_get_moments": [vp, vp, vp, vp],
         "mp_solve_host": [vp, vp, vp],
+        "mp_solve_host_async": [vp, vp, vp],
         "mp_mesh_synchronize": [vp],
         "mp_profile_enable": [vp, i],
         "mp_profile_read": [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i), dp, i, ctypes.POINTER(i)],
@@ -221,6 +222,13 @@ class Mesh:
         """End-to-end solve from host addresses (e.g. pinned torch tensors)."""
         _check(self._lib.mp_solve_host(self._h, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(phi_ptr)),
                "mp_solve_host")
+
+    def solve_host_ptr_async(self, rho_ptr: int, phi_ptr: int):
+        """Enqueue an end-to-end solve from pinned host addresses without waiting
+        (mp_solve_host_async): consecutive calls overlap one download with the next
+        upload.  The buffers stay in use until synchronize()."""
+        _check(self._lib.mp_solve_host_async(self._h, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(phi_ptr)),
+               "mp_solve_host_async")
 
     # -- per-kernel timing
     def profile(self, enable: bool = True):

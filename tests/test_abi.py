@@ -27,7 +27,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = set(declared_functions())
     for required in ("mp_mesh_create", "mp_set_density", "mp_solve", "mp_get_phi", "mp_get_moments",
-                     "mp_mesh_destroy", "mp_batch_create", "mp_batch_solve", "mp_autotune", "mp_solve_host"):
+                     "mp_mesh_destroy", "mp_batch_create", "mp_batch_solve", "mp_autotune", "mp_solve_host",
+                     "mp_solve_host_async"):
         assert required in names
 
 

@@ -96,6 +96,34 @@ def test_host_end_to_end_equals_device_solve(prec):
     assert np.array_equal(phi_h.numpy(), dev)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_async_host_solves_in_flight_equal_device_solves(prec):
+    """Five asynchronous host round trips in flight at once (two staging pairs in
+    turn, so pairs are reused while earlier downloads may still run): each output
+    equals that density's own device solve, and get_phi returns the last one."""
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    ws = [W.presn(n_r=32, n_theta=32, n_phi=64, L=8, seed=40 + k) for k in range(5)]
+    m = ws[0].mesh
+    devs = [gpu_solve(w, prec, want_moments=False)["phi"] for w in ws]
+    rhos = [torch.from_numpy(w.rho).pin_memory() for w in ws]
+    phis = [torch.full_like(r, np.nan).pin_memory() for r in rhos]
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=prec) as mesh:
+        for r, p in zip(rhos, phis):
+            mesh.solve_host_ptr_async(r.data_ptr(), p.data_ptr())
+        mesh.synchronize()
+        last = torch.empty(m.cells, dtype=torch.float64, device="cuda")
+        mesh.get_phi(last)
+        mesh.synchronize()
+        # the synchronous call after asynchronous ones reuses the same pairs
+        again = torch.empty_like(rhos[0]).pin_memory()
+        mesh.solve_host_ptr(rhos[1].data_ptr(), again.data_ptr())
+    for k in range(5):
+        assert np.array_equal(phis[k].numpy().ravel(), devs[k].ravel()), k
+    assert np.array_equal(last.cpu().numpy(), devs[4].ravel())
+    assert np.array_equal(again.numpy().ravel(), devs[1].ravel())
+
+
 def test_batch_equals_individual_solves():
     import torch
     from paper_2602_02507_gb300 import multipole as mpl
