@@ -834,7 +834,11 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
             if (is >> a >> b >> c >> d >> e >> ns_s >> ns_b >> sw >> br) {
                 std::ostringstream k;
                 k << a << ' ' << b << ' ' << c << ' ' << d << ' ' << e;
-                if (k.str() == key) {
+                // a line that does not fit this plan's reserved memory (or an odd density
+                // ring, which the converter groups cannot share) is not used
+                const bool fits = ns_s >= 2 && !(ns_s & 1) && ns_s <= m->plan.ns_s_max && ns_b >= 1 &&
+                                  ns_b <= m->plan.ns_b_max && (sw == 64 || sw == 128 || sw == 256);
+                if (k.str() == key && fits) {
                     m->plan.ns_s = ns_s;
                     m->plan.ns_b = ns_b;
                     m->plan.scan_threads = sw;
@@ -862,9 +866,10 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
         for (int sw : sws) cands.push_back({base.ns_s, base.ns_b, sw, 0});
     } else {
         // the synthesis table ring depth only matters when the table is not resident
-        const int ns_b_lo = base.b_resident ? base.ns_b : 2;
-        for (int ns_s = 3; ns_s <= base.ns_s; ++ns_s)
-            for (int ns_b = ns_b_lo; ns_b <= base.ns_b; ++ns_b)
+        const int ns_b_lo = base.b_resident ? base.ns_b_max : 2;
+        // even density-ring depths only (the converter groups alternate over its slots)
+        for (int ns_s = 2; ns_s <= base.ns_s_max; ns_s += 2)
+            for (int ns_b = ns_b_lo; ns_b <= base.ns_b_max; ++ns_b)
                 for (int br = 0; br <= 1; ++br)
                     if (br ? base.proj_res_ok : base.proj_ring_ok)
                         for (int sw : sws) cands.push_back({ns_s, ns_b, sw, br});

@@ -37,6 +37,9 @@ struct SplitPlan {
     int proj_smem = 0;    // dynamic shared memory bytes
     int synth_smem = 0;
     int ns_s = 6;         // projection: TMA stages of the density
+    int ns_o = 2;         // projection: stages of converted A operands (bf16 terms)
+    int ns_s_max = 0;     // projection: the deepest density ring the reserved shared memory holds
+    int ns_b_max = 0;     // synthesis: the deepest table ring the reserved shared memory holds
     int proj_b_resident = 0;  // projection: whole pre-split table held in shared memory
     int proj_res_ok = 0, proj_ring_ok = 0;  // projection: which table modes fit the reserved memory
     int ns_b = 3;         // synthesis: table stages (when not resident)

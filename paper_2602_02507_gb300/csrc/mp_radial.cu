@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
                                              float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL)
 {
     __shared__ double wt[2][NT / 32];
+    // the next kernel's blocks may start (and copy their tables) while this one runs
+    pdl_trigger();
     pdl_wait();  // A comes from the previous kernel
     const int q = blockIdx.x;
     int l = (int)sqrtf((float)q);
@@ -121,6 +123,8 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
                                                  float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL)
 {
     __shared__ double wt[2][NT / 32];
+    // the next kernel's blocks may start (and copy their tables) while this one runs
+    pdl_trigger();
     pdl_wait();  // A comes from the previous kernel
     const int q = blockIdx.x;
     int l = (int)sqrtf((float)q);

@@ -283,7 +283,14 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         const int row = qd * 32 + lane;
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
         int lt = 0, prev_tile = -1;
-        long long c = 0;  // CTA-wide chunk sequence number (same order as the producer and the MMA)
+        // this group converts the chunks c = grp, grp + 2, ... of the CTA-wide sequence (the
+        // producer's and the MMA's order): its ring positions advance two slots per own chunk
+        Ring rs, ro;
+        if (grp) {
+            rs.next(NS_S);
+            ro.next(NS_O);
+        }
+        int par = 0;  // parity of the CTA-wide chunk sequence number
         float sref = 0.0f, sref_prev = 0.0f;
         uint32_t efmax = 0;  // largest float64 exponent field seen (flags values beyond float32)
         bool ok = true;
@@ -341,11 +348,16 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                 sref = f64w_to_f32_fast(ref_next.x, ref_next.y, e0);
                 ref_next = load_ref(tile + gridDim.x);
             }
-            for (int it = 0; it < prm.n_kc; ++it, ++c) {
-                if ((int)(c & 1) != grp) continue;
-                const int kc = rotated_chunk(it, tile, prm.n_kc);
-                const int sidx = (int)(c % NS_S), oidx = (int)(c % NS_O);
-                const uint32_t sph = (uint32_t)((c / NS_S) & 1), oph = (uint32_t)((c / NS_O) & 1);
+            const int rot = rotated_chunk(0, tile, prm.n_kc);
+            for (int it = 0; it < prm.n_kc; ++it, par ^= 1) {
+                if (par != grp) continue;
+                const int kc = (it + rot >= prm.n_kc) ? it + rot - prm.n_kc : it + rot;
+                const int sidx = rs.idx, oidx = ro.idx;
+                const uint32_t sph = rs.phase, oph = ro.phase;
+                rs.next(NS_S);
+                rs.next(NS_S);
+                ro.next(NS_O);
+                ro.next(NS_O);
                 ok = warp_all(mbar_wait(smem_u32(&s_full[sidx]), sph, abort_flag, prm.err));
                 if (!ok) break;
                 ok = warp_all(mbar_wait(smem_u32(&o_empty[oidx]), oph ^ 1, abort_flag, prm.err));
@@ -916,9 +928,12 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
         // during the next solve's density stream)
         const uint64_t l2_first = l2_evict_first_policy();
         Ring ra;
-        uint32_t u = 0, cs = 0;
+        uint32_t u = 0;
+        int cs = 0;  // staging box of this warp in use
         bool ok = true;
+        const int nmine = (NC / 16 - quarter + 3) / 4;  // chunks quarter, quarter + 4, ...
         for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ra.next(NS_A)) {
+            const int rot = nmine > 0 ? rotated_chunk(0, tile, nmine) : 0;
             ok = warp_all(mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err));
             if (!ok) break;
             const float2 g0 = reinterpret_cast<const float2 *>(sA + (size_t)ra.idx * a_stage + prm.a_bytes)[row];
@@ -932,14 +947,13 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t tcol = tmem_base + lane_base + (uint32_t)buf * acc_stride;
-                const int nmine = (NC / 16 - quarter + 3) / 4;  // chunks quarter, quarter + 4, ...
                 for (int it = 0; it < nmine; ++it) {
-                    const int ch = quarter + 4 * rotated_chunk(it, tile, nmine);
+                    const int ch = quarter + 4 * ((it + rot >= nmine) ? it + rot - nmine : it + rot);
                     uint32_t v[16];
                     tmem_ld16(tcol + (uint32_t)(ch * 16), v);
                     tmem_ld_wait();
-                    uint8_t *st = stg + (size_t)(cw * NSTG + (cs % NSTG)) * STG_BYTES;
-                    ++cs;
+                    uint8_t *st = stg + (size_t)(cw * NSTG + cs) * STG_BYTES;
+                    if (++cs == NSTG) cs = 0;
                     if (lane == 0) {
                         if (NSTG > 1)
                             bulk_wait_read_le1();
@@ -1116,16 +1130,22 @@ int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs)
 int split_smem_limits(mp_mesh *m)
 {
     SplitPlan &pl = m->plan;
-    // projection: four density stages (more measured no faster), the table resident when it
-    // fits beside them, else a ring; fewer stages when neither fits
-    int ns_s = 0, b_res = 0;
-    for (int s = 4; s >= 2 && ns_s == 0; --s)
-        for (int r = 1; r >= 0; --r)
-            if (proj_smem_bytes(pl, s, 2, r) <= kSmemLimit) {
-                ns_s = s;
+    // projection: (density stages, A-operand stages) in order of preference, the table
+    // resident when it fits beside them, else a ring.  Both depths are even: the two
+    // converter groups take alternate chunks, so with an even depth each slot belongs to
+    // one group, and a group can never run a whole ring ahead of the other (a parity wait
+    // on a slot two phases behind would pass at once)
+    static const int kProjCfg[][2] = {{4, 2}, {2, 2}};
+    int ns_s = 0, ns_o = 0, b_res = 0;
+    for (const auto &c : kProjCfg) {
+        for (int r = 1; r >= 0 && ns_s == 0; --r)
+            if (proj_smem_bytes(pl, c[0], c[1], r) <= kSmemLimit) {
+                ns_s = c[0];
+                ns_o = c[1];
                 b_res = r;
-                break;
             }
+        if (ns_s) break;
+    }
     if (ns_s == 0) return 1;
     // synthesis: prefer the whole table resident, two A stages and double-buffered staging
     const int n_chunks = pl.n_nc * (pl.Kpad / 16);
@@ -1148,12 +1168,15 @@ int split_smem_limits(mp_mesh *m)
     }
     if (!found) return 2;
     pl.ns_s = ns_s;
+    pl.ns_s_max = ns_s;
+    pl.ns_b_max = pl.ns_b;
+    pl.ns_o = ns_o;
     pl.proj_b_resident = b_res;
-    pl.proj_res_ok = proj_smem_bytes(pl, ns_s, 2, 1) <= kSmemLimit;
-    pl.proj_ring_ok = proj_smem_bytes(pl, ns_s, 2, 0) <= kSmemLimit;
+    pl.proj_res_ok = proj_smem_bytes(pl, ns_s, ns_o, 1) <= kSmemLimit;
+    pl.proj_ring_ok = proj_smem_bytes(pl, ns_s, ns_o, 0) <= kSmemLimit;
     // the launch reserves the larger of the table modes that fit, so the tuner may switch them
-    pl.proj_smem = std::max(pl.proj_res_ok ? proj_smem_bytes(pl, ns_s, 2, 1) : 0,
-                            pl.proj_ring_ok ? proj_smem_bytes(pl, ns_s, 2, 0) : 0);
+    pl.proj_smem = std::max(pl.proj_res_ok ? proj_smem_bytes(pl, ns_s, ns_o, 1) : 0,
+                            pl.proj_ring_ok ? proj_smem_bytes(pl, ns_s, ns_o, 0) : 0);
     return 0;
 }
 
@@ -1202,7 +1225,8 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho)
     prm.Npad = pl.Npad;
     prm.n_tiles = (int)((m->R + kBM - 1) / kBM);
     prm.ns_s = pl.ns_s;
-    prm.ns_o = 2;
+    prm.ns_o = pl.ns_o;
+    if ((prm.ns_s & 1) || (prm.ns_o & 1) || prm.ns_s < 2 || prm.ns_o < 2) return cudaErrorInvalidValue;
     prm.bchunk = (uint32_t)(3 * pl.Npad * proj::BK * 2);
     prm.bload = (uint32_t)(proj_b_terms(pl) * pl.Npad * proj::BK * 2);
     prm.nacc = std::max(1, std::min(std::min(4, 256 / pl.Npad), pl.n_kc));
