@@ -263,21 +263,22 @@ __device__ __forceinline__ float f64w_to_f32(uint32_t lo, uint32_t hi)
 
 __device__ __forceinline__ bool f64w_nonfinite(uint32_t hi) { return (hi & 0x7FF00000u) == 0x7FF00000u; }
 
-// Same conversion, cheaper: the low nine exponent bits and the top 23 mantissa
-// bits come out of one 64-bit shift (after adding half a float32 ulp for
-// round-half-up); for exponents inside the float32 normal range the float32
-// exponent field is then the low eight float64 exponent bits with the top bit
-// flipped.  Magnitudes outside [2^-126, 2^128) give a signed zero; the caller
-// tracks ef = hi & 0x7FF00000 (returned) to flag values too large for float32.
+// Same conversion, cheaper, for values that are split into bf16 terms next
+// (which keep about 16 significant bits): the float32 exponent field is the low
+// eight float64 exponent bits with the top bit flipped (for exponents inside the
+// float32 normal range), and the 23 mantissa bits are the top float64 mantissa
+// bits with the lowest one forced to 1 ("jamming": at most one float32 ulp from
+// the value and, unlike truncation, without a bias toward zero).  Magnitudes
+// below 2^-126 (zeros included) give a signed zero.  Magnitudes at or above
+// 2^128 (and inf, nan) give no meaningful result: the caller tracks
+// ef = hi & 0x7FF00000 (returned) and reports them.
 __device__ __forceinline__ float f64w_to_f32_fast(uint32_t lo, uint32_t hi, uint32_t &ef)
 {
-    const unsigned long long v = ((static_cast<unsigned long long>(hi) << 32) | lo) + (1ull << 28);
-    const uint32_t t = static_cast<uint32_t>(v >> 29);
+    const uint32_t t = __funnelshift_l(lo, hi, 3);
     const uint32_t sign = hi & 0x80000000u;
-    uint32_t r = ((t & 0x7FFFFFFFu) | sign) ^ 0x40000000u;
+    const uint32_t r = (((t & 0x7FFFFFFFu) | sign) ^ 0x40000000u) | 1u;
     ef = hi & 0x7FF00000u;
-    r = (ef - (897u << 20) < (254u << 20)) ? r : sign;
-    return __uint_as_float(r);
+    return __uint_as_float(ef >= (897u << 20) ? r : sign);
 }
 
 // float64 -> float32 with integer ops (round to nearest, ties away from zero):

@@ -74,6 +74,8 @@ SPLIT_CASES = {
                                    ("bf16x3", "bf16x6")),
     "monopole_L0_8x16x32": (lambda: W.presn(n_r=8, n_theta=16, n_phi=32, L=0), ("bf16x3",)),
     "random_rough_6x32x64_L8": (lambda: W.random_small((6, 32, 64), 8, seed=8, r0=0.2, r1=1.0), ("bf16x6",)),
+    # more 128-row tiles than the projection's persistent grid has CTAs, the last tile ragged
+    "multi_wave_200x100x32_L8": (lambda: W.presn(n_r=200, n_theta=100, n_phi=32, L=8), ("bf16x3", "bf16x6")),
     # tables too large for shared memory: the direct theta contraction and the per-row
     # theta synthesis
     "high_L_fallback_4x96x64_L30": (lambda: W.presn(n_r=4, n_theta=96, n_phi=64, L=30, r_lo=1e7, r_hi=1.3e7),
