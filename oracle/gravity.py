@@ -16,10 +16,11 @@ Readings where the paper is silent (listed with R13 in the design notes):
 * Phi lives at cell centres, the coordinate midpoints of the cell edges (the
   midpoint reading of the Poisson solver), so the difference along x is
   (Phi[i+1] - Phi[i-1]) / (x_c[i+1] - x_c[i-1]) on any (non-uniform) mesh.
-* phi is periodic (the mesh spans [0, 2 pi]): the neighbours of the first and
-  last azimuthal cells wrap around, their coordinate shifted by 2 pi.  With one
-  azimuthal cell the phi derivative is zero; with two, both neighbours are the
-  same cell and the difference is zero.
+* phi is periodic when the azimuthal edges span 2 pi: the neighbours of the
+  first and last azimuthal cells wrap around, their coordinate shifted by 2 pi.
+  With one azimuthal cell the phi derivative is zero; with two, both neighbours
+  are the same cell and the difference is zero.  A mesh spanning less than 2 pi
+  is treated like r and theta at its ends.
 * At the first and last cell along r and theta the two nearest cells along that
   coordinate are the cell itself and its one neighbour: a one-sided difference.
   With one cell along the coordinate the derivative is zero.
@@ -28,7 +29,8 @@ Pins (tests/test_oracle_gravity.py): a potential linear in r_c has the exact
 derivative everywhere, edges included; -1/r_c on a geometric mesh has the
 closed-form interior difference 1/(r_c[i+1] r_c[i-1]); cos(phi_c) and
 cos(theta_c) on uniform meshes have the closed forms -sin(x) sin(h)/h (the
-azimuthal wrap included) and the one-sided edge values; a potential of r alone
+azimuthal wrap included) and the one-sided edge values (also at the ends of an
+azimuthal range short of 2 pi); a potential of r alone
 gives zero theta and phi components and E = v^r S_r; one cell along an axis
 gives a zero component.
 """
@@ -73,7 +75,9 @@ def gradient(phi, r_edges, theta_edges, phi_edges) -> np.ndarray:
     centred difference over the two nearest cells along each coordinate."""
     phi = np.asarray(phi, dtype=np.float64)
     out = np.zeros((3,) + phi.shape)
-    for axis, (edges, periodic) in enumerate(((r_edges, False), (theta_edges, False), (phi_edges, True))):
+    pe = np.asarray(phi_edges, dtype=np.float64)
+    full_circle = abs((pe[-1] - pe[0]) - 2.0 * np.pi) <= 1e-12 * 2.0 * np.pi
+    for axis, (edges, periodic) in enumerate(((r_edges, False), (theta_edges, False), (phi_edges, full_circle))):
         lo, hi, dx = stencil(edges, periodic)
         for i in range(lo.size):
             if dx[i] == 0.0:

@@ -110,3 +110,16 @@ def test_energy_source_of_a_separable_potential_uses_all_three_components():
     inner = slice(1, -1)  # interior polar cells (the poles are one-sided)
     assert np.allclose(s["E"][:, inner], want[:, inner], rtol=1e-12, atol=1e-13)
     assert np.allclose(s["S"][2], -rho * g_p, rtol=1e-12, atol=1e-13)
+
+
+def test_azimuthal_range_short_of_a_full_circle_is_one_sided_at_its_ends():
+    n_p = 8
+    ph = np.linspace(0.0, np.pi, n_p + 1)  # half a circle
+    r, th, _ = _mesh(n_r=2, n_t=3, n_p=n_p)
+    pc = O.centres(ph)
+    h = np.pi / n_p
+    phi = np.broadcast_to(np.cos(pc)[None, None, :], (2, 3, n_p)).copy()
+    g = O.gradient(phi, r, th, ph)[2][0, 0]
+    assert np.allclose(g[1:-1], -np.sin(pc[1:-1]) * np.sin(h) / h, rtol=0, atol=1e-14)
+    assert np.isclose(g[0], (np.cos(pc[1]) - np.cos(pc[0])) / h, rtol=1e-13)
+    assert np.isclose(g[-1], (np.cos(pc[-1]) - np.cos(pc[-2])) / h, rtol=1e-13)
