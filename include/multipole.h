@@ -224,6 +224,33 @@ MP_API mp_status mp_batch_destroy(mp_batch *batch);
 MP_API mp_status mp_autotune(mp_mesh *mesh, const char *cache_path);
 
 /*
+ * Gravitational source terms of the fluid balance equations (Sec. 3,
+ * Eq. (BalancedVariablesGravitational)) from a potential on this mesh:
+ *   grad[a] = d(Phi)/dx^a, x = (r, theta, phi)   (coordinate derivatives)
+ *   S[a]    = -rho grad[a]                        (momentum source, covariant)
+ *   E       = -rho (v^r grad[0] + v^theta grad[1] + v^phi grad[2])  (energy source)
+ * Each derivative is the centred difference over the two nearest cells along
+ * the coordinate (the rule Sec. 3 states with the sources), with cell centres
+ * at coordinate midpoints: (Phi[hi] - Phi[lo]) / (x_c[hi] - x_c[lo]).  phi
+ * wraps around when the azimuthal edges span 2 pi; at the ends of r, theta (and
+ * of a shorter azimuthal range) the two nearest cells are the cell and its one
+ * neighbour.  One cell along a coordinate, or two azimuthal cells on a full
+ * circle, give a zero derivative.
+ *   phi_dev  [n_r][n_theta][n_phi] float64, device; NULL: the last solve's Phi
+ *   rho_dev  same layout; NULL: the bound density
+ *   v_dev    [3][n_r][n_theta][n_phi] (v^r, v^theta, v^phi), or NULL
+ *   grad_dev, S_dev [3][n_r][n_theta][n_phi]; E_dev [n_r][n_theta][n_phi]:
+ *            outputs, each may be NULL (not all; E_dev needs v_dev); they must
+ *            not overlap the inputs
+ * All buffers are caller-owned device memory; nothing is allocated.  Float64
+ * arithmetic whatever the mesh precision.  Enqueued on the mesh's stream;
+ * argument errors return at once (MP_ERR_INVALID_ARG, or MP_ERR_NOT_READY when
+ * phi_dev is NULL before any solve or rho_dev is NULL with no bound density).
+ */
+MP_API mp_status mp_gravity_sources(mp_mesh *mesh, const double *phi_dev, const double *rho_dev, const double *v_dev,
+                                    double *grad_dev, double *S_dev, double *E_dev);
+
+/*
  * Device rate probes (diagnostics, not part of a solve): measures, on the
  * current device, the float64 FMA rate in TFLOP/s (the roofline of the float64
  * path) and the hardware float64 -> float32 conversion rate in conversions/s.

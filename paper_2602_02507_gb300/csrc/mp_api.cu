@@ -156,7 +156,7 @@ static void free_mesh_buffers(mp_mesh *m)
                     m->d_GR,  m->d_GI,   m->d_V,      m->d_A,     m->d_MR,     m->d_MI,    m->d_C,
                     m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_Ith32, m->d_Itc32, m->d_Itc0, m->d_C0, m->d_colsum,
                     m->d_tabB, m->d_tabT, m->d_Aop, m->d_G0, m->phi_own, m->h_rho[0], m->h_rho[1],
-                    m->h_phi[0], m->h_phi[1], m->d_err};
+                    m->h_phi[0], m->h_phi[1], m->d_err, m->d_gst};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &pe : m->prof_pending) {
@@ -470,6 +470,8 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
         }
         st = cuda_status(cudaStreamSynchronize(m->stream), "table build");
         if (st != MP_OK) return fail(st);
+        st = cuda_status(gravity_prepare(m), "gravity stencils");
+        if (st != MP_OK) return fail(st);
     }
     *out = m;
     return MP_OK;
@@ -562,6 +564,25 @@ mp_status mp_get_phi(mp_mesh *m, double *phi_dev)
     if (src == phi_dev) return MP_OK;
     DeviceGuard dg(m->device);
     MP_TRY(cudaMemcpyAsync(phi_dev, src, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    return MP_OK;
+}
+
+mp_status mp_gravity_sources(mp_mesh *m, const double *phi_dev, const double *rho_dev, const double *v_dev,
+                             double *grad_dev, double *S_dev, double *E_dev)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    if (!grad_dev && !S_dev && !E_dev) return set_error(MP_ERR_INVALID_ARG, "no output requested");
+    if (E_dev && !v_dev) return set_error(MP_ERR_INVALID_ARG, "the energy source needs the velocity");
+    if (!phi_dev) {
+        if (!m->solved || !m->last_phi) return set_error(MP_ERR_NOT_READY, "no solve has run");
+        phi_dev = m->last_phi;
+    }
+    if (!rho_dev) {
+        if (!m->rho) return set_error(MP_ERR_NOT_READY, "no density bound");
+        rho_dev = m->rho;
+    }
+    DeviceGuard dg(m->device);
+    MP_TRY(launch_gravity(m, phi_dev, rho_dev, v_dev, grad_dev, S_dev, E_dev));
     return MP_OK;
 }
 

@@ -49,6 +49,13 @@ struct SplitPlan {
     int scan_threads = 128;  // radial recurrences: threads (shell chunks) per moment column
 };
 
+// Centred difference along one axis at one cell: (Phi[hi] - Phi[lo]) * w, w = 1 / (x_c[hi] - x_c[lo])
+// (0 where the derivative is zero)
+struct GradStencil {
+    int lo, hi;
+    double w;
+};
+
 struct ProfileEntry {
     const char *name = nullptr;
     int launches = 0;
@@ -99,6 +106,7 @@ struct mp_mesh {
     float *d_G0 = nullptr;        // [tiles * 128] x (hi, lo) float pairs: m = 0 column of the theta synthesis
     float2 *d_Itc0 = nullptr;     // [L+1][n_t] Ith[tri(l,0)][j] / dmu_j as (hi, lo) float pairs
     float2 *d_C0 = nullptr;       // [n_r][L+1] m = 0 coefficients C[i][l^2] as (hi, lo) float pairs
+    mp::GradStencil *d_gst = nullptr;  // gravity sources: [n_r + n_theta + n_phi] difference stencils
     uint8_t *d_tabB = nullptr;    // projection B operand, bf16 x 3 terms, canonical layout
     uint8_t *d_tabT = nullptr;    // synthesis B operand, bf16 x 3 terms, canonical layout
     size_t tabB_chunk_bytes = 0, tabT_chunk_bytes = 0;
@@ -186,6 +194,11 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho);
 cudaError_t launch_split_theta(mp_mesh *m);
 cudaError_t launch_split_synth(mp_mesh *m, double *phi);
 int split_smem_limits(mp_mesh *m);  // 0 when the plan fits, else an error
+
+// ---- gravitational source terms ----
+cudaError_t gravity_prepare(mp_mesh *m);  // stencils from the host edges (once per mesh)
+cudaError_t launch_gravity(mp_mesh *m, const double *phi, const double *rho, const double *v, double *grad,
+                           double *S, double *E);
 
 // profiling hooks used by the launchers
 void prof_begin(mp_mesh *m, const char *name, cudaEvent_t *ev_start);

@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
         "mp_last_error_detail": [ctypes.c_char_p, i],
         "mp_probe_rates": [dp, dp],
         "mp_moments_noalloc": [vp, vp, vp],
+        "mp_gravity_sources": [vp, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -198,6 +199,16 @@ class Mesh:
         p = [None if t is None else ctypes.c_void_p(_tensor_ptr(t, s, nm))
              for t, s, nm in ((ang, n_r * K, "ang"), (mr, (n_r + 1) * K, "mr"), (mi, (n_r + 1) * K, "mi"))]
         _check(self._lib.mp_get_moments(self._h, *p), "mp_get_moments")
+
+    def gravity_sources(self, phi=None, rho=None, v=None, grad=None, S=None, E=None):
+        """Gravitational source terms (mp_gravity_sources): grad / S [3 * cells] and E
+        [cells] CUDA float64 tensors (any may be None); phi / rho None: the last solve's
+        potential / the bound density; v [3 * cells] contravariant velocity."""
+        n = self.cells
+        args = [None if t is None else ctypes.c_void_p(_tensor_ptr(t, size, name))
+                for t, size, name in ((phi, n, "phi"), (rho, n, "rho"), (v, 3 * n, "v"),
+                                      (grad, 3 * n, "grad"), (S, 3 * n, "S"), (E, n, "E"))]
+        _check(self._lib.mp_gravity_sources(self._h, *args), "mp_gravity_sources")
 
     def moments_noalloc(self, rho, out):
         """Angular moments of rho into out [n_r * K_L] without device allocation
