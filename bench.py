@@ -365,6 +365,32 @@ def run_ours(args):
 
     rates = mpl.probe_rates()
 
+    # ---- gravitational source terms (Sec. 3) of this solve's potential: momentum S and
+    # energy E from a synthetic velocity; float64, bound by the float64 pipe
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    gvel = torch.randn(3 * cells, dtype=torch.float64, device="cuda", generator=gen)
+    gS = torch.empty(3 * cells, dtype=torch.float64, device="cuda")
+    gE = torch.empty(cells, dtype=torch.float64, device="cuda")
+    kg = max(3, min(args.steps // 200, 50))
+    for _ in range(2):
+        mesh.gravity_sources(v=gvel, S=gS, E=gE)
+    mesh.synchronize()
+    e0.record(stream)
+    for _ in range(kg):
+        mesh.gravity_sources(v=gvel, S=gS, E=gE)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_us = max_over_ranks(e0.elapsed_time(e1)) / kg * 1e3
+    fp64_instr_peak = rates["fp64_tflops"] * 1e12 / 2.0  # one FMA instruction = 2 flops
+    gravity = {"kernel": "gravity_sources", "launches": kg, "avg_launch_us": g_us,
+               "algorithmic_bytes_per_cell": 72, "hbm_gbs": 72 * cells / g_us / 1e3,
+               "hbm_frac": 72 * cells / g_us / 1e3 / measured_peaks()[0],
+               "fp64_instr_per_cell": 12, "fp64_instr_per_s": 12 * cells / (g_us * 1e-6),
+               "fp64_frac": 12 * cells / (g_us * 1e-6) / fp64_instr_peak, "bound": "fp64",
+               "note": "S [3] and E from Phi, rho, v [3]: 9 float64 reads + 4 writes per cell"}
+    del gvel, gS, gE
+
     # ---- roofline of the dominant kernel
     log("kernels:", json.dumps(prof))
     dom = max(prof, key=lambda k: prof[k]["total_ms"])
@@ -402,6 +428,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": 8 * cells, "steps": ke, "max_abs_diff_vs_device_solve": e2e_err},
             # kernels of the split chain per solve (one graph launch each) x timed solves
             "gpu_launches": len(prof) * args.steps,
+            "gravity_sources": gravity,
             "device_rates": {"fp64_tflops_measured": rates["fp64_tflops"],
                              "cvt_f64_to_f32_per_s_measured": rates["cvt_f64_f32_per_s"]},
             "clocks": clk,
