@@ -202,6 +202,67 @@ def spheroid_fraction(r_edges, theta_edges, a1: float, a3: float, sub: int = 16)
     return frac
 
 
+def spheroid_fraction_exact(r_edges, theta_edges, a1: float, a3: float) -> np.ndarray:
+    """Exact volume fraction [n_r, n_theta] of each (axisymmetric) cell inside the oblate
+    spheroid r_perp^2/a1^2 + z^2/a3^2 < 1 (a1 >= a3).  With mu = cos(theta) the surface
+    radius is R(mu) = (A + B mu^2)^(-1/2), A = 1/a1^2, B = 1/a3^2 - 1/a1^2, and the part of
+    cell (i, j) inside is (2 pi / 3) int [clamp(R^3, r_i^3, r_{i+1}^3) - r_i^3] d(mu) over
+    the cell's mu range.  The clamp changes form where R(mu) = r_i or r_{i+1}
+    (mu^2 = (1/r^2 - A) / B); between those points R^3 integrates in closed form,
+    int (A + B mu^2)^(-3/2) d(mu) = mu / (A sqrt(A + B mu^2))."""
+    r = np.asarray(r_edges, float)
+    th = np.asarray(theta_edges, float)
+    n_r, n_t = r.size - 1, th.size - 1
+    A = 1.0 / (a1 * a1)
+    B = 1.0 / (a3 * a3) - A
+
+    def R3(mu):
+        return (A + B * mu * mu) ** -1.5
+
+    def F(mu):  # antiderivative of R^3
+        return mu / (A * math.sqrt(A + B * mu * mu))
+
+    def crossings(rad):
+        if B <= 0.0:
+            return []
+        m2 = (1.0 / (rad * rad) - A) / B
+        if m2 <= 0.0 or m2 >= 1.0:
+            return []
+        m = math.sqrt(m2)
+        return [-m, m]
+
+    frac = np.zeros((n_r, n_t))
+    r_in, r_out = a3, a1  # the surface lies between these radii
+    for j in range(n_t):
+        mu_a, mu_b = sorted((math.cos(th[j]), math.cos(th[j + 1])))
+        # surface radii over the cell's polar range: extremes at its ends or at mu = 0
+        cand = [R3(mu_a) ** (1 / 3), R3(mu_b) ** (1 / 3)]
+        if mu_a < 0.0 < mu_b:
+            cand.append(a1)
+        Rmin, Rmax = max(min(cand), r_in * (1 - 1e-15)), min(max(cand), r_out * (1 + 1e-15))
+        for i in range(n_r):
+            lo, hi = r[i], r[i + 1]
+            if hi <= Rmin:
+                frac[i, j] = 1.0
+                continue
+            if lo >= Rmax:
+                continue
+            lo3, hi3 = lo ** 3, hi ** 3
+            pts = sorted({mu_a, mu_b, *[m for rad in (lo, hi) if rad > 0.0 for m in crossings(rad)
+                                         if mu_a < m < mu_b]})
+            vol = 0.0
+            for u0, u1 in zip(pts[:-1], pts[1:]):
+                mid = R3(0.5 * (u0 + u1))
+                if mid <= lo3:
+                    continue
+                if mid >= hi3:
+                    vol += (hi3 - lo3) * (u1 - u0)
+                else:
+                    vol += F(u1) - F(u0) - lo3 * (u1 - u0)
+            frac[i, j] = vol / ((hi3 - lo3) * (mu_b - mu_a))
+    return frac
+
+
 def spheroid(n_r=64, n_theta=32, n_phi=64, L=8, a1=1.0, a3=0.6, rho0=1.0, r_max=1.5) -> Workload:
     r = uniform_edges(0.0, r_max, n_r)
     th, ph = angular_edges(n_theta, n_phi)
