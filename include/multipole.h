@@ -251,6 +251,32 @@ MP_API mp_status mp_gravity_sources(mp_mesh *mesh, const double *phi_dev, const 
                                     double *grad_dev, double *S_dev, double *E_dev);
 
 /*
+ * Coarsening-block averaging (Sec. 2.1, where angular cell widths fall below the
+ * minimum radial width cells are grouped into angular blocks at each radius;
+ * Sec. 2.3, each cell of a block takes the block's volume-weighted mean
+ * sum V_j K_j / sum V_j, which conserves the block's integral).  Blocks, a reading
+ * of the paper's figures: with Delta r_min the smallest radial width and widths at
+ * the cell-centre radius r_c, polar blocks are runs of p cells, p the smallest
+ * power of two dividing n_theta with p r_c min(dtheta) >= Delta r_min (else the
+ * whole polar range); within a polar block, azimuthal blocks are runs of q cells,
+ * q the smallest power of two dividing n_phi with q r_c sin(theta_c) min(dphi) >=
+ * Delta r_min for the block's cell nearest the axis (else the whole ring).
+ *   fields_dev  n_fields device arrays of [n_r][n_theta][n_phi] float64, the f-th
+ *               at fields_dev + f * field_stride; averaged in place (cells outside
+ *               every block are not touched)
+ * Float64; nothing is allocated; enqueued on the mesh's stream.
+ */
+MP_API mp_status mp_coarsen(mp_mesh *mesh, double *fields_dev, int n_fields, long long field_stride);
+
+/*
+ * The block sizes of mp_coarsen (host arrays, caller-owned; either may be NULL):
+ * c_theta [n_r] polar block size per shell, c_phi [n_r][n_theta] azimuthal block
+ * size of each cell's polar block (the coarsening factors c_i of the CFL time
+ * step, Sec. 2.3).
+ */
+MP_API mp_status mp_coarsening_factors(const mp_mesh *mesh, int *c_theta, int *c_phi);
+
+/*
  * Device rate probes (diagnostics, not part of a solve): measures, on the
  * current device, the float64 FMA rate in TFLOP/s (the roofline of the float64
  * path) and the hardware float64 -> float32 conversion rate in conversions/s.

@@ -156,7 +156,7 @@ static void free_mesh_buffers(mp_mesh *m)
                     m->d_GR,  m->d_GI,   m->d_V,      m->d_A,     m->d_MR,     m->d_MI,    m->d_C,
                     m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_Ith32, m->d_Itc32, m->d_Itc0, m->d_C0, m->d_colsum,
                     m->d_tabB, m->d_tabT, m->d_Aop, m->d_G0, m->phi_own, m->h_rho[0], m->h_rho[1],
-                    m->h_phi[0], m->h_phi[1], m->d_err, m->d_gst};
+                    m->h_phi[0], m->h_phi[1], m->d_err, m->d_gst, m->d_cwork, m->d_cweights};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &pe : m->prof_pending) {
@@ -472,6 +472,8 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
         if (st != MP_OK) return fail(st);
         st = cuda_status(gravity_prepare(m), "gravity stencils");
         if (st != MP_OK) return fail(st);
+        st = cuda_status(coarsen_prepare(m), "coarsening blocks");
+        if (st != MP_OK) return fail(st);
     }
     *out = m;
     return MP_OK;
@@ -583,6 +585,27 @@ mp_status mp_gravity_sources(mp_mesh *m, const double *phi_dev, const double *rh
     }
     DeviceGuard dg(m->device);
     MP_TRY(launch_gravity(m, phi_dev, rho_dev, v_dev, grad_dev, S_dev, E_dev));
+    return MP_OK;
+}
+
+mp_status mp_coarsen(mp_mesh *m, double *fields_dev, int n_fields, long long field_stride)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    if (n_fields < 0 || n_fields > 65535) return set_error(MP_ERR_INVALID_ARG, "n_fields must be in [0, 65535]");
+    if (n_fields == 0) return MP_OK;
+    if (!fields_dev) return set_error(MP_ERR_INVALID_ARG, "fields_dev is NULL");
+    if (n_fields > 1 && field_stride < m->N)
+        return set_error(MP_ERR_INVALID_ARG, "field_stride must be at least n_r * n_theta * n_phi");
+    DeviceGuard dg(m->device);
+    MP_TRY(launch_coarsen(m, fields_dev, n_fields, field_stride));
+    return MP_OK;
+}
+
+mp_status mp_coarsening_factors(const mp_mesh *m, int *c_theta, int *c_phi)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    if (c_theta) std::copy(m->h_ctheta.begin(), m->h_ctheta.end(), c_theta);
+    if (c_phi) std::copy(m->h_cphi.begin(), m->h_cphi.end(), c_phi);
     return MP_OK;
 }
 

@@ -1,0 +1,215 @@
+// mp_coarsen.cu -- coarsening-block averaging (GenASiS II Sec. 2.1: angular blocks
+// where angular cell widths fall below the minimum radial width; Sec. 2.3: every
+// cell of a block takes the volume-weighted mean sum V_j K_j / sum V_j).
+//
+// Block rule (the paper shows the blocks only in figures):
+//   Delta r_min = the smallest radial width; widths at the cell-centre radius r_c.
+//   polar: runs of p cells, p the smallest power of two dividing n_theta with
+//          p r_c min(dtheta) >= Delta r_min, else the whole polar range;
+//   azimuthal, within a polar block: runs of q cells, q the smallest power of two
+//          dividing n_phi with q r_c sin(theta_c) min(dphi) >= Delta r_min (theta_c
+//          of the block's polar cell nearest the axis), else the whole ring.
+// Volumes are separable, so within a shell the weights are dmu_j dphi_k.
+//
+// The host turns the rule into a work list once per mesh: one entry per polar
+// block that is coarsened (p > 1 or q > 1); cells outside every block are not
+// touched.  One CTA per (entry, field).  Azimuthal blocks of a power of two up to
+// 64 cells: threads run along phi two columns at a time (16-byte accesses), each
+// sums its columns over the polar block, and the block's lanes add their
+// weighted sums by shuffles (weights normalised on the host); wider blocks: the
+// whole CTA reduces each one.  Every coarsened cell is read once and written once.  Float64
+// throughout.
+#include <cmath>
+
+#include "mp_internal.h"
+#include "ptx.cuh"
+
+namespace mp {
+
+namespace {
+
+constexpr int kCoarsenThreads = 256;
+constexpr int kCoarsenLevels = 7;  // azimuthal block sizes 1, 2, 4, ..., 64 have normalised weights
+
+// The block's mean is sum_j sum_k (dmu_j / sum dmu) (dphi_k / sum_{block} dphi) K_jk: the
+// normalised azimuthal weights nph[level][k] (block size 2^level) come from the host.
+__global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict__ f, long long stride,
+                                                             const int4 *__restrict__ work,
+                                                             const double *__restrict__ dmu,
+                                                             const double *__restrict__ dph,
+                                                             const double *__restrict__ nph, int n_t, int n_p,
+                                                             int vec2)
+{
+    const int4 wk = work[blockIdx.x];  // shell, first polar cell, polar size, azimuthal size
+    const int j0 = wk.y, ct = wk.z, cp = wk.w;
+    double *base = f + (long long)blockIdx.y * stride + ((long long)wk.x * n_t + j0) * n_p;
+    const int lane = threadIdx.x & 31;
+    const bool pow2 = (cp & (cp - 1)) == 0;
+    if (pow2 && vec2 && cp <= 64) {
+        // two adjacent columns per thread (16-byte accesses along phi): each sums its columns
+        // over the polar block; the cp / 2 lanes of an azimuthal block (aligned: 64 columns
+        // per warp, a multiple of cp) add their weighted sums by shuffles
+        const double *w_phi = nph + (size_t)(__ffs(cp) - 1) * n_p;
+        for (int k0 = 0; k0 < n_p; k0 += 2 * kCoarsenThreads) {
+            const int k = k0 + 2 * threadIdx.x;
+            const bool in = k < n_p;
+            double c0 = 0.0, c1 = 0.0, wsum = 0.0;
+            if (in)
+                for (int j = 0; j < ct; ++j) {
+                    const double2 v = *reinterpret_cast<const double2 *>(base + (long long)j * n_p + k);
+                    const double w = dmu[j0 + j];
+                    c0 = fma(w, v.x, c0);
+                    c1 = fma(w, v.y, c1);
+                    wsum += w;
+                }
+            double2 out;
+            if (cp == 1) {
+                out = make_double2(c0 / wsum, c1 / wsum);
+            } else {
+                double num = in ? fma(w_phi[k + 1], c1, w_phi[k] * c0) : 0.0;
+                for (int o = 1; o < cp / 2; o <<= 1) num += __shfl_xor_sync(0xFFFFFFFFu, num, o);
+                out = make_double2(num / wsum, num / wsum);
+            }
+            if (in)
+                for (int j = 0; j < ct; ++j) *reinterpret_cast<double2 *>(base + (long long)j * n_p + k) = out;
+        }
+        return;
+    }
+    if (pow2 && cp <= 32) {
+        // one column per thread (odd n_phi or unaligned fields)
+        const double *w_phi = nph + (size_t)(__ffs(cp) - 1) * n_p;
+        for (int k0 = 0; k0 < n_p; k0 += kCoarsenThreads) {
+            const int k = k0 + threadIdx.x;
+            const bool in = k < n_p;
+            double col = 0.0, wsum = 0.0;
+            if (in)
+                for (int j = 0; j < ct; ++j) {
+                    col = fma(dmu[j0 + j], base[(long long)j * n_p + k], col);
+                    wsum += dmu[j0 + j];
+                }
+            double num = in ? w_phi[k] * col : 0.0;
+            for (int o = 1; o < cp; o <<= 1) num += __shfl_xor_sync(0xFFFFFFFFu, num, o);
+            if (in) {
+                const double mean = num / wsum;
+                for (int j = 0; j < ct; ++j) base[(long long)j * n_p + k] = mean;
+            }
+        }
+        return;
+    }
+    // wider (or uneven) azimuthal blocks: the whole CTA reduces each block, its threads
+    // striding along phi within every polar row (coalesced)
+    __shared__ double red[2][kCoarsenThreads / 32];
+    __shared__ double bmean;
+    const int warp = threadIdx.x >> 5;
+    for (int kb = 0; kb < n_p / cp; ++kb) {
+        double num = 0.0, den = 0.0;
+        for (int j = 0; j < ct; ++j) {
+            const double wj = dmu[j0 + j];
+            for (int kk = threadIdx.x; kk < cp; kk += kCoarsenThreads) {
+                const int k = kb * cp + kk;
+                const double w = wj * dph[k];
+                num = fma(w, base[(long long)j * n_p + k], num);
+                den += w;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xFFFFFFFFu, num, o);
+            den += __shfl_xor_sync(0xFFFFFFFFu, den, o);
+        }
+        if (lane == 0) {
+            red[0][warp] = num;
+            red[1][warp] = den;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double n_ = 0.0, d_ = 0.0;
+            for (int w = 0; w < kCoarsenThreads / 32; ++w) {
+                n_ += red[0][w];
+                d_ += red[1][w];
+            }
+            bmean = n_ / d_;
+        }
+        __syncthreads();
+        const double mean = bmean;
+        for (int j = 0; j < ct; ++j)
+            for (int kk = threadIdx.x; kk < cp; kk += kCoarsenThreads) base[(long long)j * n_p + kb * cp + kk] = mean;
+        __syncthreads();  // red and bmean are reused by the next block
+    }
+}
+
+int pow2_block(double need, int n)
+{
+    for (int p = 1; p <= n; p *= 2)
+        if (n % p == 0 && (double)p >= need) return p;
+    return n;
+}
+
+}  // namespace
+
+cudaError_t coarsen_prepare(mp_mesh *m)
+{
+    const int n_r = m->n_r, n_t = m->n_t, n_p = m->n_p;
+    double dr_min = m->h_r[1] - m->h_r[0], dth = m->h_th[1] - m->h_th[0], dph = m->h_ph[1] - m->h_ph[0];
+    for (int i = 1; i < n_r; ++i) dr_min = std::min(dr_min, m->h_r[i + 1] - m->h_r[i]);
+    for (int j = 1; j < n_t; ++j) dth = std::min(dth, m->h_th[j + 1] - m->h_th[j]);
+    for (int k = 1; k < n_p; ++k) dph = std::min(dph, m->h_ph[k + 1] - m->h_ph[k]);
+    m->h_ctheta.assign(n_r, 1);
+    m->h_cphi.assign((size_t)n_r * n_t, 1);
+    std::vector<int4> work;
+    for (int i = 0; i < n_r; ++i) {
+        const double rc = 0.5 * (m->h_r[i] + m->h_r[i + 1]);
+        const int ct = pow2_block(dr_min / (rc * dth), n_t);
+        m->h_ctheta[i] = ct;
+        for (int j0 = 0; j0 < n_t; j0 += ct) {
+            double need = 0.0;  // the block's cell nearest the axis needs the widest azimuthal block
+            for (int j = j0; j < j0 + ct; ++j) {
+                const double tc = 0.5 * (m->h_th[j] + m->h_th[j + 1]);
+                need = std::max(need, dr_min / (rc * std::sin(tc) * dph));
+            }
+            const int cp = pow2_block(need, n_p);
+            for (int j = j0; j < j0 + ct; ++j) m->h_cphi[(size_t)i * n_t + j] = cp;
+            if (ct > 1 || cp > 1) work.push_back(make_int4(i, j0, ct, cp));
+        }
+    }
+    m->n_cwork = (int)work.size();
+    // weights: dmu [n_t], dphi [n_p], then per block size 2^level the normalised dphi
+    std::vector<double> w((size_t)n_t + (size_t)n_p * (1 + kCoarsenLevels), 0.0);
+    for (int j = 0; j < n_t; ++j) w[j] = std::cos(m->h_th[j]) - std::cos(m->h_th[j + 1]);
+    for (int k = 0; k < n_p; ++k) w[(size_t)n_t + k] = m->h_ph[k + 1] - m->h_ph[k];
+    for (int lv = 0; lv < kCoarsenLevels; ++lv) {
+        const int q = 1 << lv;
+        if (n_p % q) continue;  // no blocks of this size on this mesh
+        for (int k0 = 0; k0 < n_p; k0 += q) {
+            double sum = 0.0;
+            for (int k = k0; k < k0 + q; ++k) sum += w[(size_t)n_t + k];
+            for (int k = k0; k < k0 + q; ++k)
+                w[(size_t)n_t + (size_t)n_p * (1 + lv) + k] = w[(size_t)n_t + k] / sum;
+        }
+    }
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&m->d_cwork), std::max<size_t>(1, work.size()) * sizeof(int4));
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(reinterpret_cast<void **>(&m->d_cweights), w.size() * sizeof(double));
+    if (e != cudaSuccess) return e;
+    m->device_bytes += std::max<size_t>(1, work.size()) * sizeof(int4) + w.size() * sizeof(double);
+    if (!work.empty()) {
+        e = cudaMemcpy(m->d_cwork, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaMemcpy(m->d_cweights, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice);
+}
+
+cudaError_t launch_coarsen(mp_mesh *m, double *fields, int n_fields, long long stride)
+{
+    if (m->n_cwork == 0 || n_fields == 0) return cudaSuccess;
+    cudaEvent_t ev;
+    prof_begin(m, "coarsen_blocks", &ev);
+    // 16-byte accesses need even n_phi and 16-byte aligned fields
+    const int vec2 = (m->n_p % 2 == 0) && (reinterpret_cast<uintptr_t>(fields) % 16 == 0) && (stride % 2 == 0);
+    k_coarsen<<<dim3((unsigned)m->n_cwork, (unsigned)n_fields), kCoarsenThreads, 0, m->stream>>>(
+        fields, stride, m->d_cwork, m->d_cweights, m->d_cweights + m->n_t, m->d_cweights + m->n_t + m->n_p, m->n_t,
+        m->n_p, vec2);
+    prof_end(m, "coarsen_blocks", ev);
+    return cudaGetLastError();
+}
+
+}  // namespace mp

@@ -107,6 +107,13 @@ struct mp_mesh {
     float2 *d_Itc0 = nullptr;     // [L+1][n_t] Ith[tri(l,0)][j] / dmu_j as (hi, lo) float pairs
     float2 *d_C0 = nullptr;       // [n_r][L+1] m = 0 coefficients C[i][l^2] as (hi, lo) float pairs
     mp::GradStencil *d_gst = nullptr;  // gravity sources: [n_r + n_theta + n_phi] difference stencils
+    // coarsening blocks: per shell the polar block size, per (shell, polar cell) the azimuthal
+    // one; the device work list (shell, first polar cell, polar size, azimuthal size) of the
+    // coarsened polar blocks and the weights dmu [n_theta], dphi [n_phi]
+    std::vector<int> h_ctheta, h_cphi;
+    int4 *d_cwork = nullptr;
+    int n_cwork = 0;
+    double *d_cweights = nullptr;
     uint8_t *d_tabB = nullptr;    // projection B operand, bf16 x 3 terms, canonical layout
     uint8_t *d_tabT = nullptr;    // synthesis B operand, bf16 x 3 terms, canonical layout
     size_t tabB_chunk_bytes = 0, tabT_chunk_bytes = 0;
@@ -199,6 +206,10 @@ int split_smem_limits(mp_mesh *m);  // 0 when the plan fits, else an error
 cudaError_t gravity_prepare(mp_mesh *m);  // stencils from the host edges (once per mesh)
 cudaError_t launch_gravity(mp_mesh *m, const double *phi, const double *rho, const double *v, double *grad,
                            double *S, double *E);
+
+// ---- coarsening blocks ----
+cudaError_t coarsen_prepare(mp_mesh *m);  // block sizes and work list from the host edges (once per mesh)
+cudaError_t launch_coarsen(mp_mesh *m, double *fields, int n_fields, long long stride);
 
 // profiling hooks used by the launchers
 void prof_begin(mp_mesh *m, const char *name, cudaEvent_t *ev_start);

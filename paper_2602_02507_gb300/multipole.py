@@ -72,6 +72,8 @@ def load_library(path: str = LIB_PATH):
         "mp_probe_rates": [dp, dp],
         "mp_moments_noalloc": [vp, vp, vp],
         "mp_gravity_sources": [vp, vp, vp, vp, vp, vp, vp],
+        "mp_coarsen": [vp, vp, ctypes.c_int, ctypes.c_longlong],
+        "mp_coarsening_factors": [vp, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -209,6 +211,27 @@ class Mesh:
                 for t, size, name in ((phi, n, "phi"), (rho, n, "rho"), (v, 3 * n, "v"),
                                       (grad, 3 * n, "grad"), (S, 3 * n, "S"), (E, n, "E"))]
         _check(self._lib.mp_gravity_sources(self._h, *args), "mp_gravity_sources")
+
+    def coarsen(self, fields, n_fields: int = 1, field_stride: int | None = None):
+        """Coarsening-block averaging in place (mp_coarsen) of n_fields float64 fields of
+        cells values each, the f-th at offset f * field_stride in the CUDA tensor."""
+        stride = self.cells if field_stride is None else int(field_stride)
+        need = (n_fields - 1) * stride + self.cells if n_fields > 0 else 0
+        import torch
+        if not isinstance(fields, torch.Tensor) or not fields.is_cuda or fields.dtype != torch.float64:
+            raise TypeError("fields must be a CUDA float64 tensor")
+        if not fields.is_contiguous() or fields.numel() < need:
+            raise ValueError(f"fields must be contiguous with at least {need} elements")
+        _check(self._lib.mp_coarsen(self._h, ctypes.c_void_p(fields.data_ptr()), int(n_fields), stride), "mp_coarsen")
+
+    def coarsening_factors(self):
+        """(c_theta [n_r], c_phi [n_r][n_theta]) block sizes of the coarsening."""
+        n_r, n_t = self.shape[0], self.shape[1]
+        ct = np.zeros(n_r, dtype=np.int32)
+        cp = np.zeros((n_r, n_t), dtype=np.int32)
+        _check(self._lib.mp_coarsening_factors(self._h, ctypes.c_void_p(ct.ctypes.data),
+                                               ctypes.c_void_p(cp.ctypes.data)), "mp_coarsening_factors")
+        return ct, cp
 
     def moments_noalloc(self, rho, out):
         """Angular moments of rho into out [n_r * K_L] without device allocation
