@@ -96,44 +96,69 @@ __global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict_
         }
         return;
     }
-    // wider (or uneven) azimuthal blocks: the whole CTA reduces each block, its threads
-    // striding along phi within every polar row (coalesced)
-    __shared__ double red[2][kCoarsenThreads / 32];
-    __shared__ double bmean;
-    const int warp = threadIdx.x >> 5;
-    for (int kb = 0; kb < n_p / cp; ++kb) {
+    // wider blocks (a power of two above 64, or the whole ring): threads again take columns
+    // along phi (two at a time when aligned) and sum them over the polar block; each warp
+    // reduces its chunk of 32 V columns, and one thread per azimuthal block adds its chunks
+    // in order (a chunk never straddles two blocks: cp is a multiple of 32 V, or the block
+    // is the whole ring)
+    extern __shared__ double chunk[];  // per chunk of 32 V columns: num, den; then per block: the mean
+    const int V = vec2 ? 2 : 1, per_warp = 32 * V, warp = threadIdx.x >> 5;
+    const int n_chunks = (n_p + per_warp - 1) / per_warp;
+    for (int k0 = 0; k0 < n_p; k0 += V * kCoarsenThreads) {
+        const int k = k0 + V * threadIdx.x;
+        double c0 = 0.0, c1 = 0.0, wsum = 0.0;
+        if (k < n_p)
+            for (int j = 0; j < ct; ++j) {
+                const double w = dmu[j0 + j];
+                if (V == 2) {
+                    const double2 v = *reinterpret_cast<const double2 *>(base + (long long)j * n_p + k);
+                    c0 = fma(w, v.x, c0);
+                    c1 = fma(w, v.y, c1);
+                } else {
+                    c0 = fma(w, base[(long long)j * n_p + k], c0);
+                }
+                wsum += w;
+            }
         double num = 0.0, den = 0.0;
-        for (int j = 0; j < ct; ++j) {
-            const double wj = dmu[j0 + j];
-            for (int kk = threadIdx.x; kk < cp; kk += kCoarsenThreads) {
-                const int k = kb * cp + kk;
-                const double w = wj * dph[k];
-                num = fma(w, base[(long long)j * n_p + k], num);
-                den += w;
+        if (k < n_p) {
+            num = dph[k] * c0;
+            den = dph[k] * wsum;
+            if (V == 2) {
+                num = fma(dph[k + 1], c1, num);
+                den = fma(dph[k + 1], wsum, den);
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
             num += __shfl_xor_sync(0xFFFFFFFFu, num, o);
             den += __shfl_xor_sync(0xFFFFFFFFu, den, o);
         }
-        if (lane == 0) {
-            red[0][warp] = num;
-            red[1][warp] = den;
+        const int ci = (k0 + warp * per_warp) / per_warp;
+        if (lane == 0 && ci < n_chunks) {
+            chunk[ci] = num;
+            chunk[n_chunks + ci] = den;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double n_ = 0.0, d_ = 0.0;
-            for (int w = 0; w < kCoarsenThreads / 32; ++w) {
-                n_ += red[0][w];
-                d_ += red[1][w];
-            }
-            bmean = n_ / d_;
+    }
+    __syncthreads();
+    const int nkb = n_p / cp, cpc = (cp + per_warp - 1) / per_warp;  // chunks per block
+    for (int b = threadIdx.x; b < nkb; b += kCoarsenThreads) {
+        double n_ = 0.0, d_ = 0.0;
+        for (int c = b * cpc; c < min((b + 1) * cpc, n_chunks); ++c) {
+            n_ += chunk[c];
+            d_ += chunk[n_chunks + c];
         }
-        __syncthreads();
-        const double mean = bmean;
-        for (int j = 0; j < ct; ++j)
-            for (int kk = threadIdx.x; kk < cp; kk += kCoarsenThreads) base[(long long)j * n_p + kb * cp + kk] = mean;
-        __syncthreads();  // red and bmean are reused by the next block
+        chunk[2 * n_chunks + b] = n_ / d_;
+    }
+    __syncthreads();
+    for (int k0 = 0; k0 < n_p; k0 += V * kCoarsenThreads) {
+        const int k = k0 + V * threadIdx.x;
+        if (k >= n_p) continue;
+        const double mean = chunk[2 * n_chunks + k / cp];
+        for (int j = 0; j < ct; ++j) {
+            if (V == 2)
+                *reinterpret_cast<double2 *>(base + (long long)j * n_p + k) = make_double2(mean, mean);
+            else
+                base[(long long)j * n_p + k] = mean;
+        }
     }
 }
 
@@ -205,7 +230,11 @@ cudaError_t launch_coarsen(mp_mesh *m, double *fields, int n_fields, long long s
     prof_begin(m, "coarsen_blocks", &ev);
     // 16-byte accesses need even n_phi and 16-byte aligned fields
     const int vec2 = (m->n_p % 2 == 0) && (reinterpret_cast<uintptr_t>(fields) % 16 == 0) && (stride % 2 == 0);
-    k_coarsen<<<dim3((unsigned)m->n_cwork, (unsigned)n_fields), kCoarsenThreads, 0, m->stream>>>(
+    // wide blocks keep per-chunk sums and per-block means in dynamic shared memory
+    const int per_warp = vec2 ? 64 : 32;
+    const int n_chunks = (m->n_p + per_warp - 1) / per_warp;
+    const size_t smem = (size_t)3 * n_chunks * sizeof(double);  // blocks here span whole chunks
+    k_coarsen<<<dim3((unsigned)m->n_cwork, (unsigned)n_fields), kCoarsenThreads, smem, m->stream>>>(
         fields, stride, m->d_cwork, m->d_cweights, m->d_cweights + m->n_t, m->d_cweights + m->n_t + m->n_p, m->n_t,
         m->n_p, vec2);
     prof_end(m, "coarsen_blocks", ev);
