@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict_
                                                              const int4 *__restrict__ work,
                                                              const double *__restrict__ dmu,
                                                              const double *__restrict__ dph,
-                                                             const double *__restrict__ nph, int n_t, int n_p,
+                                                             const double *__restrict__ nph,
+                                                             const double *__restrict__ inv_mu, int n_t, int n_p,
                                                              int vec2)
 {
     const int4 wk = work[blockIdx.x];  // shell, first polar cell, polar size, azimuthal size
@@ -45,6 +46,8 @@ __global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict_
     double *base = f + (long long)blockIdx.y * stride + ((long long)wk.x * n_t + j0) * n_p;
     const int lane = threadIdx.x & 31;
     const bool pow2 = (cp & (cp - 1)) == 0;
+    const double inv = inv_mu[blockIdx.x];  // 1 / sum of dmu over the polar block (no divisions here:
+                                            // they are slow on the float64 pipe of this part)
     if (pow2 && vec2 && cp <= 64) {
         // two adjacent columns per thread (16-byte accesses along phi): each sums its columns
         // over the polar block; the cp / 2 lanes of an azimuthal block (aligned: 64 columns
@@ -53,22 +56,21 @@ __global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict_
         for (int k0 = 0; k0 < n_p; k0 += 2 * kCoarsenThreads) {
             const int k = k0 + 2 * threadIdx.x;
             const bool in = k < n_p;
-            double c0 = 0.0, c1 = 0.0, wsum = 0.0;
+            double c0 = 0.0, c1 = 0.0;
             if (in)
                 for (int j = 0; j < ct; ++j) {
                     const double2 v = *reinterpret_cast<const double2 *>(base + (long long)j * n_p + k);
                     const double w = dmu[j0 + j];
                     c0 = fma(w, v.x, c0);
                     c1 = fma(w, v.y, c1);
-                    wsum += w;
                 }
             double2 out;
             if (cp == 1) {
-                out = make_double2(c0 / wsum, c1 / wsum);
+                out = make_double2(c0 * inv, c1 * inv);
             } else {
                 double num = in ? fma(w_phi[k + 1], c1, w_phi[k] * c0) : 0.0;
                 for (int o = 1; o < cp / 2; o <<= 1) num += __shfl_xor_sync(0xFFFFFFFFu, num, o);
-                out = make_double2(num / wsum, num / wsum);
+                out = make_double2(num * inv, num * inv);
             }
             if (in)
                 for (int j = 0; j < ct; ++j) *reinterpret_cast<double2 *>(base + (long long)j * n_p + k) = out;
@@ -81,16 +83,13 @@ __global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict_
         for (int k0 = 0; k0 < n_p; k0 += kCoarsenThreads) {
             const int k = k0 + threadIdx.x;
             const bool in = k < n_p;
-            double col = 0.0, wsum = 0.0;
+            double col = 0.0;
             if (in)
-                for (int j = 0; j < ct; ++j) {
-                    col = fma(dmu[j0 + j], base[(long long)j * n_p + k], col);
-                    wsum += dmu[j0 + j];
-                }
+                for (int j = 0; j < ct; ++j) col = fma(dmu[j0 + j], base[(long long)j * n_p + k], col);
             double num = in ? w_phi[k] * col : 0.0;
             for (int o = 1; o < cp; o <<= 1) num += __shfl_xor_sync(0xFFFFFFFFu, num, o);
             if (in) {
-                const double mean = num / wsum;
+                const double mean = num * inv;
                 for (int j = 0; j < ct; ++j) base[(long long)j * n_p + k] = mean;
             }
         }
@@ -106,7 +105,7 @@ __global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict_
     const int n_chunks = (n_p + per_warp - 1) / per_warp;
     for (int k0 = 0; k0 < n_p; k0 += V * kCoarsenThreads) {
         const int k = k0 + V * threadIdx.x;
-        double c0 = 0.0, c1 = 0.0, wsum = 0.0;
+        double c0 = 0.0, c1 = 0.0;
         if (k < n_p)
             for (int j = 0; j < ct; ++j) {
                 const double w = dmu[j0 + j];
@@ -117,15 +116,14 @@ __global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict_
                 } else {
                     c0 = fma(w, base[(long long)j * n_p + k], c0);
                 }
-                wsum += w;
             }
-        double num = 0.0, den = 0.0;
+        double num = 0.0, den = 0.0;  // den: the block's dphi sum
         if (k < n_p) {
             num = dph[k] * c0;
-            den = dph[k] * wsum;
+            den = dph[k];
             if (V == 2) {
                 num = fma(dph[k + 1], c1, num);
-                den = fma(dph[k + 1], wsum, den);
+                den += dph[k + 1];
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -146,7 +144,7 @@ __global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict_
             n_ += chunk[c];
             d_ += chunk[n_chunks + c];
         }
-        chunk[2 * n_chunks + b] = n_ / d_;
+        chunk[2 * n_chunks + b] = n_ / d_ * inv;  // one division per block
     }
     __syncthreads();
     for (int k0 = 0; k0 < n_p; k0 += V * kCoarsenThreads) {
@@ -197,8 +195,15 @@ cudaError_t coarsen_prepare(mp_mesh *m)
         }
     }
     m->n_cwork = (int)work.size();
-    // weights: dmu [n_t], dphi [n_p], then per block size 2^level the normalised dphi
-    std::vector<double> w((size_t)n_t + (size_t)n_p * (1 + kCoarsenLevels), 0.0);
+    std::vector<double> inv_mu(std::max<size_t>(1, work.size()), 0.0);
+    for (size_t e = 0; e < work.size(); ++e) {
+        double sum = 0.0;
+        for (int j = work[e].y; j < work[e].y + work[e].z; ++j) sum += std::cos(m->h_th[j]) - std::cos(m->h_th[j + 1]);
+        inv_mu[e] = 1.0 / sum;
+    }
+    // weights: dmu [n_t], dphi [n_p], per block size 2^level the normalised dphi, then per work
+    // entry 1 / (sum of dmu over its polar block)
+    std::vector<double> w((size_t)n_t + (size_t)n_p * (1 + kCoarsenLevels) + inv_mu.size(), 0.0);
     for (int j = 0; j < n_t; ++j) w[j] = std::cos(m->h_th[j]) - std::cos(m->h_th[j + 1]);
     for (int k = 0; k < n_p; ++k) w[(size_t)n_t + k] = m->h_ph[k + 1] - m->h_ph[k];
     for (int lv = 0; lv < kCoarsenLevels; ++lv) {
@@ -211,6 +216,7 @@ cudaError_t coarsen_prepare(mp_mesh *m)
                 w[(size_t)n_t + (size_t)n_p * (1 + lv) + k] = w[(size_t)n_t + k] / sum;
         }
     }
+    std::copy(inv_mu.begin(), inv_mu.end(), w.begin() + n_t + (size_t)n_p * (1 + kCoarsenLevels));
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&m->d_cwork), std::max<size_t>(1, work.size()) * sizeof(int4));
     if (e != cudaSuccess) return e;
     e = cudaMalloc(reinterpret_cast<void **>(&m->d_cweights), w.size() * sizeof(double));
@@ -235,8 +241,8 @@ cudaError_t launch_coarsen(mp_mesh *m, double *fields, int n_fields, long long s
     const int n_chunks = (m->n_p + per_warp - 1) / per_warp;
     const size_t smem = (size_t)3 * n_chunks * sizeof(double);  // blocks here span whole chunks
     k_coarsen<<<dim3((unsigned)m->n_cwork, (unsigned)n_fields), kCoarsenThreads, smem, m->stream>>>(
-        fields, stride, m->d_cwork, m->d_cweights, m->d_cweights + m->n_t, m->d_cweights + m->n_t + m->n_p, m->n_t,
-        m->n_p, vec2);
+        fields, stride, m->d_cwork, m->d_cweights, m->d_cweights + m->n_t, m->d_cweights + m->n_t + m->n_p,
+        m->d_cweights + m->n_t + (size_t)m->n_p * (1 + kCoarsenLevels), m->n_t, m->n_p, vec2);
     prof_end(m, "coarsen_blocks", ev);
     return cudaGetLastError();
 }
