@@ -25,6 +25,9 @@ MESHES = {
     "paper_2d_48": lambda: W.paper_mesh(48, 0.25, 3.68, 0, 2),
     "offset_geometric_3d": lambda: W.Mesh(np.geomspace(1e5, 1e7, 41), np.linspace(0, np.pi, 21),
                                           np.linspace(0, 2 * np.pi, 41), 0, 1.0, "geo"),
+    # 640 azimuthal cells (2^7 x 5): whole-ring blocks wider than one pass of the CTA
+    "wide_rings_6x8x640": lambda: W.Mesh(np.linspace(0.0, 1.0, 7), np.linspace(0, np.pi, 9),
+                                         np.linspace(0, 2 * np.pi, 641), 0, 1.0, "wide"),
 }
 
 
