@@ -366,6 +366,97 @@ __global__ void __launch_bounds__(1024, 1) k32_theta_pipe(const float *__restric
 // float32 over blocks of eight cells, block sums with Kahan compensation.
 constexpr int kMgShells = 32, kMgCols = 2 * kMgShells, kMgRows = 64, kMgK = 32, kMgLd = kMgK + 4;
 
+// One pass of degree tile [l0, l0 + 16 RT) of order m: thread (rg, cg) owns degrees
+// rg + 16 a (a < RT) and columns cg + 16 b (b < 4).  The tile has only as many rows as
+// the order has degrees left (rounded up to 16): an order m has L + 1 - m degrees, so a
+// fixed 64-row tile would mostly multiply zeros at high m.
+template <int RT>
+__device__ __forceinline__ void theta_mg_pass(float (*sT)[kMgLd], float (*sF)[kMgLd], const float *__restrict__ F,
+                                              const float *__restrict__ Ith, double *__restrict__ A, int n_r, int n_t,
+                                              int KL, int P, int ldF, double scale, int m, int i0, int nl, int pc,
+                                              int l0)
+{
+    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+    float s[RT][4], c[RT][4];
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) s[a][b] = c[a][b] = 0.0f;
+    // the next chunk's global loads go out before the current chunk's arithmetic (registers
+    // hold them in between): a 256-thread block moves at most 2 + 2 float4 per thread
+    constexpr int kT = (16 * RT * (kMgK / 4) + 255) / 256, kF = kMgCols * (kMgK / 4) / 256;
+    float4 pt[kT], pf[kF];
+    auto load_chunk = [&](int j0) {
+#pragma unroll
+        for (int n = 0; n < kT; ++n) {
+            const int e = tid + 256 * n, r = e >> 3, q = e & 7, j = j0 + 4 * q;
+            pt[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < 16 * RT * (kMgK / 4) && l0 + r < nl && j < ldF)
+                pt[n] = __ldg(reinterpret_cast<const float4 *>(Ith + (size_t)tri(m + l0 + r, m) * ldF + j));
+        }
+#pragma unroll
+        for (int n = 0; n < kF; ++n) {
+            const int e = tid + 256 * n, col = e >> 3, q = e & 7, j = j0 + 4 * q;
+            const int i = i0 + (col >> 1), sn = col & 1;
+            pf[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n_r && j < ldF && (sn == 0 || m > 0))
+                pf[n] = __ldg(reinterpret_cast<const float4 *>(F + ((size_t)i * P + pc + sn) * ldF + j));
+        }
+    };
+    load_chunk(0);
+    for (int j0 = 0; j0 < n_t; j0 += kMgK) {
+        __syncthreads();  // the previous chunk is consumed
+#pragma unroll
+        for (int n = 0; n < kT; ++n) {
+            const int e = tid + 256 * n;
+            if (e < 16 * RT * (kMgK / 4)) *reinterpret_cast<float4 *>(&sT[e >> 3][4 * (e & 7)]) = pt[n];
+        }
+#pragma unroll
+        for (int n = 0; n < kF; ++n) {
+            const int e = tid + 256 * n;
+            *reinterpret_cast<float4 *>(&sF[e >> 3][4 * (e & 7)]) = pf[n];
+        }
+        __syncthreads();
+        if (j0 + kMgK < n_t) load_chunk(j0 + kMgK);
+#pragma unroll
+        for (int jb = 0; jb < kMgK; jb += 8) {
+            float blk[RT][4];
+#pragma unroll
+            for (int a = 0; a < RT; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) blk[a][b] = 0.0f;
+#pragma unroll
+            for (int jj = jb; jj < jb + 8; jj += 4) {
+                float4 t[RT], f[4];
+#pragma unroll
+                for (int a = 0; a < RT; ++a) t[a] = *reinterpret_cast<const float4 *>(&sT[rg + 16 * a][jj]);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) f[b] = *reinterpret_cast<const float4 *>(&sF[cg + 16 * b][jj]);
+#pragma unroll
+                for (int a = 0; a < RT; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) blk[a][b] = dot4(t[a], f[b], blk[a][b]);
+            }
+#pragma unroll
+            for (int a = 0; a < RT; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) kahan_add(s[a][b], c[a][b], blk[a][b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < RT; ++a) {
+        const int lr = l0 + rg + 16 * a;
+        if (lr >= nl) continue;
+        const int l = m + lr;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int col = cg + 16 * b, i = i0 + (col >> 1), sn = col & 1;
+            if (i < n_r && (sn == 0 || m > 0))
+                A[(size_t)i * KL + l * l + pc + sn] = scale * f32_to_f64_alu(s[a][b] - c[a][b]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k32_theta_mgemm(const float *__restrict__ F, const float *__restrict__ Ith,
                                                        double *__restrict__ A, int n_r, int n_t, int L, int KL, int P,
                                                        int ldF, double scale)
@@ -376,66 +467,12 @@ __global__ void __launch_bounds__(256) k32_theta_mgemm(const float *__restrict__
     const int m = blockIdx.y, i0 = blockIdx.x * kMgShells;
     const int nl = L + 1 - m;
     const int pc = (m == 0) ? 0 : 2 * m - 1;
-    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
     for (int l0 = 0; l0 < nl; l0 += kMgRows) {
-        float s[4][4], c[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) s[a][b] = c[a][b] = 0.0f;
-        for (int j0 = 0; j0 < n_t; j0 += kMgK) {
-            __syncthreads();  // the previous chunk is consumed
-            for (int e = tid; e < kMgRows * (kMgK / 4); e += blockDim.x) {
-                const int r = e >> 3, q = e & 7, j = j0 + 4 * q;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (l0 + r < nl && j < ldF) v = *reinterpret_cast<const float4 *>(Ith + (size_t)tri(m + l0 + r, m) * ldF + j);
-                *reinterpret_cast<float4 *>(&sT[r][4 * q]) = v;
-            }
-            for (int e = tid; e < kMgCols * (kMgK / 4); e += blockDim.x) {
-                const int col = e >> 3, q = e & 7, j = j0 + 4 * q;
-                const int i = i0 + (col >> 1), sn = col & 1;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < n_r && j < ldF && (sn == 0 || m > 0))
-                    v = *reinterpret_cast<const float4 *>(F + ((size_t)i * P + pc + sn) * ldF + j);
-                *reinterpret_cast<float4 *>(&sF[col][4 * q]) = v;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int jb = 0; jb < kMgK; jb += 8) {
-                float blk[4][4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) blk[a][b] = 0.0f;
-#pragma unroll
-                for (int jj = jb; jj < jb + 8; jj += 4) {
-                    float4 t[4], f[4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) t[a] = *reinterpret_cast<const float4 *>(&sT[rg + 16 * a][jj]);
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) f[b] = *reinterpret_cast<const float4 *>(&sF[cg + 16 * b][jj]);
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) blk[a][b] = dot4(t[a], f[b], blk[a][b]);
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) kahan_add(s[a][b], c[a][b], blk[a][b]);
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int lr = l0 + rg + 16 * a;
-            if (lr >= nl) continue;
-            const int l = m + lr;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int col = cg + 16 * b, i = i0 + (col >> 1), sn = col & 1;
-                if (i < n_r && (sn == 0 || m > 0))
-                    A[(size_t)i * KL + l * l + pc + sn] = scale * f32_to_f64_alu(s[a][b] - c[a][b]);
-            }
+        switch (min(4, (nl - l0 + 15) / 16)) {
+        case 1: theta_mg_pass<1>(sT, sF, F, Ith, A, n_r, n_t, KL, P, ldF, scale, m, i0, nl, pc, l0); break;
+        case 2: theta_mg_pass<2>(sT, sF, F, Ith, A, n_r, n_t, KL, P, ldF, scale, m, i0, nl, pc, l0); break;
+        case 3: theta_mg_pass<3>(sT, sF, F, Ith, A, n_r, n_t, KL, P, ldF, scale, m, i0, nl, pc, l0); break;
+        default: theta_mg_pass<4>(sT, sF, F, Ith, A, n_r, n_t, KL, P, ldF, scale, m, i0, nl, pc, l0); break;
         }
     }
 }
