@@ -647,13 +647,16 @@ __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict
 
 // Theta synthesis for tables that exceed shared memory, one GEMM per order m:
 //   G[i, j][p] = sum_{l = m..L} Itc[tri(l,m)][j] C32[i][l^2 + p],   p in {pc, ps},
-// M = polar cells, N = shells (cos and sin together), K = degrees.  Block (64 polar
-// cells, 32 shells, m) stages the table rows and the coefficients of K chunks of 32
-// degrees in shared memory; thread (rg, cg) owns cells cg + 16 a (a < 4) and shells
-// rg + 16 b (b < 2), cos and sin.  The results leave as the bf16 terms of the canonical
-// MMA layout ((cos, sin) pairs, 4 bytes per term) or, for m = 0, the float32 column G0;
-// K columns past 2L keep the zeros the buffer was created with.
-constexpr int kGmCells = 64, kGmShells = 32, kGmK = 32;
+// M = polar cells, N = shells (cos and sin together), K = degrees.  Block (128 polar
+// cells, 64 shells, m) stages the table rows and the coefficients of K chunks of 32
+// degrees in shared memory, the next chunk's loads in flight (registers) during the
+// current chunk's arithmetic; thread (rg, cg) owns cells cg + 16 a (a < 8) and shells
+// rg + 16 b (b < 4), cos and sin: 64 multiply-adds per 16 shared-memory reads.  The
+// results leave as the bf16 terms of the canonical MMA layout ((cos, sin) pairs, 4 bytes
+// per term); the m = 0 column (double-float) is shared by kGm0Parts blocks per tile and
+// leaves as float32 (hi, lo) pairs.  K columns past 2L keep the zeros the buffer was
+// created with.
+constexpr int kGmCells = 128, kGmShells = 64, kGmK = 32, kGm0Parts = 4;
 
 template <int A_TERMS>
 __global__ void __launch_bounds__(256) k_gsynth_mgemm(const float *__restrict__ C32, const float *__restrict__ Itc,
@@ -664,10 +667,11 @@ __global__ void __launch_bounds__(256) k_gsynth_mgemm(const float *__restrict__ 
     __shared__ __align__(16) float sT[kGmK][kGmCells + 4];
     __shared__ float sC[kGmK][2 * kGmShells + 1];
     pdl_wait();  // C32 comes from the previous kernel
-    const int j0 = blockIdx.x * kGmCells, i0 = blockIdx.y * kGmShells, m = blockIdx.z;
-    if (m == 0) {
-        // the m = 0 column in double-float (block-uniform branch)
-        for (int e = threadIdx.x; e < kGmCells * kGmShells; e += blockDim.x) {
+    const int j0 = blockIdx.x * kGmCells, i0 = blockIdx.y * kGmShells, z = blockIdx.z;
+    if (z < kGm0Parts) {
+        // the m = 0 column in double-float (block-uniform branch), a quarter of the tile per block
+        constexpr int per = kGmCells * kGmShells / kGm0Parts;
+        for (int e = z * per + (int)threadIdx.x; e < (z + 1) * per; e += blockDim.x) {
             const int j = j0 + e % kGmCells, i = i0 + e / kGmCells;
             if (j < n_t && i < n_r)
                 *reinterpret_cast<float2 *>(G0 + 2 * ((size_t)i * n_t + j)) =
@@ -675,40 +679,57 @@ __global__ void __launch_bounds__(256) k_gsynth_mgemm(const float *__restrict__ 
         }
         return;
     }
+    const int m = z - kGm0Parts + 1;
     const int nl = L + 1 - m;
-    const int pc = (m == 0) ? 0 : 2 * m - 1;
+    const int pc = 2 * m - 1;
     const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
-    float gc[4][2], gs[4][2];
+    float gc[8][4], gs[8][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) gc[a][b] = gs[a][b] = 0.0f;
-    for (int l0 = 0; l0 < nl; l0 += kGmK) {
-        __syncthreads();
-        for (int e = tid; e < kGmK * (kGmCells / 4); e += blockDim.x) {
-            const int r = e >> 4, q = e & 15, j = j0 + 4 * q;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (l0 + r < nl && j < ldF) v = *reinterpret_cast<const float4 *>(Itc + (size_t)tri(m + l0 + r, m) * ldF + j);
-            *reinterpret_cast<float4 *>(&sT[r][4 * q]) = v;
+        for (int b = 0; b < 4; ++b) gc[a][b] = gs[a][b] = 0.0f;
+    // per chunk a thread moves 4 float4 of the table and 16 coefficients
+    float4 pt[4];
+    float pcf[16];
+    auto load_chunk = [&](int l0) {
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const int e = tid + 256 * n, r = e >> 5, q = e & 31, j = j0 + 4 * q;
+            pt[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (l0 + r < nl && j < ldF) pt[n] = __ldg(reinterpret_cast<const float4 *>(Itc + (size_t)tri(m + l0 + r, m) * ldF + j));
         }
-        for (int e = tid; e < kGmK * 2 * kGmShells; e += blockDim.x) {
-            const int r = e / (2 * kGmShells), col = e % (2 * kGmShells);
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+            const int e = tid + 256 * n, r = e >> 7, col = e & 127;
             const int i = i0 + (col >> 1), sn = col & 1, l = m + l0 + r;
-            float v = 0.0f;
-            if (l0 + r < nl && i < n_r && (sn == 0 || m > 0)) v = __ldg(C32 + (size_t)i * KL + l * l + pc + sn);
-            sC[r][col] = v;
+            pcf[n] = (l0 + r < nl && i < n_r) ? __ldg(C32 + (size_t)i * KL + l * l + pc + sn) : 0.0f;
+        }
+    };
+    load_chunk(0);
+    for (int l0 = 0; l0 < nl; l0 += kGmK) {
+        __syncthreads();  // the previous chunk is consumed
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const int e = tid + 256 * n;
+            *reinterpret_cast<float4 *>(&sT[e >> 5][4 * (e & 31)]) = pt[n];
+        }
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+            const int e = tid + 256 * n;
+            sC[e >> 7][e & 127] = pcf[n];
         }
         __syncthreads();
+        if (l0 + kGmK < nl) load_chunk(l0 + kGmK);
         const int kn = min(kGmK, nl - l0);
         for (int r = 0; r < kn; ++r) {
-            float t[4];
+            float t[8];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) t[a] = sT[r][cg + 16 * a];
+            for (int a = 0; a < 8; ++a) t[a] = sT[r][cg + 16 * a];
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < 4; ++b) {
                 const float cc = sC[r][2 * (rg + 16 * b)], cs = sC[r][2 * (rg + 16 * b) + 1];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
+                for (int a = 0; a < 8; ++a) {
                     gc[a][b] = fmaf(t[a], cc, gc[a][b]);
                     gs[a][b] = fmaf(t[a], cs, gs[a][b]);
                 }
@@ -717,11 +738,11 @@ __global__ void __launch_bounds__(256) k_gsynth_mgemm(const float *__restrict__ 
     }
     const size_t a_term_bytes = (size_t)128 * Kpad * 2;
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 4; ++b) {
         const int i = i0 + rg + 16 * b;
         if (i >= n_r) continue;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < 8; ++a) {
             const int j = j0 + cg + 16 * a;
             if (j >= n_t) continue;
             const long long row = (long long)i * n_t + j;
@@ -1273,7 +1294,9 @@ cudaError_t launch_split_synth(mp_mesh *m, double *phi)
                        m->d_C0, m->d_Itc0, m->d_Aop, m->d_G0, m->d_err, m->n_r, m->n_t, m->L, m->KL, pl.Kpad,
                        pl.ldF, tab_bytes);
     } else {
-        const dim3 grid((m->n_t + kGmCells - 1) / kGmCells, (m->n_r + kGmShells - 1) / kGmShells, m->L + 1);
+        // z < kGm0Parts: the m = 0 column; z >= kGm0Parts: order m = z - kGm0Parts + 1
+        const dim3 grid((m->n_t + kGmCells - 1) / kGmCells, (m->n_r + kGmShells - 1) / kGmShells,
+                        m->L + kGm0Parts);
         if (pl.a_terms == 2)
             launch_pdl(k_gsynth_mgemm<2>, grid, dim3(256), 0, m->stream, m->d_C32, m->d_Itc32, m->d_C0, m->d_Itc0,
                        m->d_Aop, m->d_G0,
