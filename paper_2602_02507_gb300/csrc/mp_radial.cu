@@ -184,6 +184,101 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
     }
 }
 
+// The same recurrences for four adjacent moment columns per block (used when there are
+// many columns): thread t owns column q0 + (t & 3) and shells [c CH, (c + 1) CH) with
+// c = t >> 2, so the four columns of a shell row sit in one 32-byte sector of A, MR, MI
+// and C (one column per block reads a quarter of every sector it touches).  The block
+// scans run over the lanes of one column (stride 4 within a warp), then over the warps.
+template <int NT, int CH>
+__global__ void __launch_bounds__(4 * NT) k_scan_q4(const double *__restrict__ A, const double *__restrict__ WR,
+                                                    const double *__restrict__ WI, const double *__restrict__ GR,
+                                                    const double *__restrict__ GI, double *__restrict__ MR,
+                                                    double *__restrict__ MI, double *__restrict__ C,
+                                                    float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL)
+{
+    constexpr int NW = 4 * NT / 32;
+    __shared__ double wt[2][NW][4];
+    pdl_trigger();
+    pdl_wait();  // A comes from the previous kernel
+    const int sub = threadIdx.x & 3, c = threadIdx.x >> 2, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = 4 * blockIdx.x + sub;
+    const bool valid = q < KL;
+    int l = (int)sqrtf((float)(valid ? q : 0));
+    const int qq = valid ? q : 0;
+    while (l * l > qq) --l;
+    while ((l + 1) * (l + 1) <= qq) ++l;
+    const int p = qq - l * l;
+    const int m = pcol_m(p);
+    const int Lp1 = (int)sqrtf((float)KL + 0.5f);  // L + 1
+    const int i0 = c * CH;
+    const double *wr = WR + (size_t)l * n_r;
+    const double *wi = WI + (size_t)l * n_r;
+    const double *gr = GR + (size_t)l * n_r;
+    const double *gi = GI + (size_t)l * n_r;
+    // registers hold the column's values and its inward edge moments; the small weight
+    // tables are read again where needed (cache hits), which keeps 512 threads resident
+    double a[CH];
+    double sR = 0.0, sI = 0.0;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        const int i = i0 + k;
+        const bool in = valid && i < n_r;
+        a[k] = in ? A[(size_t)i * KL + q] : 0.0;
+        if (in) {
+            sR = fma(__ldg(wr + i), a[k], sR);
+            sI = fma(__ldg(wi + i), a[k], sI);
+        }
+    }
+    // inclusive scans over the 8 chunks of this column in the warp (lanes sub, sub + 4, ...)
+    double inf = sR, inb = sI;
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+        const double yf = __shfl_up_sync(kFull, inf, o);
+        const double yb = __shfl_down_sync(kFull, inb, o);
+        if (lane >= o) inf += yf;
+        if (lane + o < 32) inb += yb;
+    }
+    double ef = __shfl_up_sync(kFull, inf, 4);
+    double eb = __shfl_down_sync(kFull, inb, 4);
+    if (lane < 4) ef = 0.0;
+    if (lane >= 28) eb = 0.0;
+    if (lane >= 28) wt[0][w][sub] = inf;
+    if (lane < 4) wt[1][w][sub] = inb;
+    __syncthreads();
+    double of = 0.0, ob = 0.0;
+    for (int w2_ = 0; w2_ < w; ++w2_) of += wt[0][w2_][sub];
+    for (int w2_ = NW - 1; w2_ > w; --w2_) ob += wt[1][w2_][sub];
+    if (!valid) return;
+    double ei[CH + 1];
+    ei[CH] = ob + eb;
+#pragma unroll
+    for (int k = CH - 1; k >= 0; --k) {
+        const int i = i0 + k;
+        ei[k] = (i < n_r) ? fma(__ldg(wi + i), a[k], ei[k + 1]) : ei[k + 1];
+    }
+    double er = of + ef;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+        const int i = i0 + k;
+        if (i < n_r) {
+            const double er1 = fma(__ldg(wr + i), a[k], er);
+            MR[(size_t)i * KL + q] = er;
+            MI[(size_t)i * KL + q] = ei[k];
+            double cv = fma(__ldg(gi + i), er + er1, __ldg(gr + i) * (ei[k] + ei[k + 1]));
+            if (m > 0) cv += cv;
+            C[(size_t)i * KL + q] = cv;
+            if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(cv);
+            if (C0 && p == 0) C0[(size_t)i * Lp1 + l] = f32_pair(cv);
+            er = er1;
+        }
+    }
+    if (c == NT - 1) {
+        // the last chunk ends at or beyond the last shell: its final values are the totals
+        MR[(size_t)n_r * KL + q] = er;
+        MI[(size_t)n_r * KL + q] = ei[CH];
+    }
+}
+
 // Split path, theta part of step (a):
 //   A[i][q] = 4 pi G sum_j Ith[t(l,m)][j] F[i][p][j],   q = l^2 + p, m = m(p)
 // F holds each shell as P rows of polar cells ([n_r][P][ldF]; ldF = n_t rounded
@@ -507,12 +602,34 @@ static bool scan_reg_dispatch(mp_mesh *m, int want_f32)
     return true;
 }
 
+// Four columns per block when there are at least four such blocks per SM; 128 chunk
+// threads per column (512 per block), CH shells each.
+static bool scan_q4_dispatch(mp_mesh *m, int want_f32)
+{
+    if (m->KL < 16 * m->num_sms) return false;
+    const int ch = (m->n_r + 127) / 128;
+    auto go = [&](auto kern) {
+        launch_pdl(kern, dim3((m->KL + 3) / 4), dim3(512), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
+                   m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, want_f32 ? m->d_C0 : nullptr, m->n_r,
+                   m->KL);
+    };
+    if (ch <= 4)
+        go(k_scan_q4<128, 4>);
+    else if (ch <= 8)
+        go(k_scan_q4<128, 8>);
+    else if (ch <= 16)
+        go(k_scan_q4<128, 16>);
+    else
+        return false;
+    return true;
+}
+
 cudaError_t launch_scan(mp_mesh *m, int want_f32)
 {
     cudaEvent_t ev;
     prof_begin(m, "radial_scan", &ev);
-    bool done;
-    switch (m->plan.scan_threads) {
+    bool done = scan_q4_dispatch(m, want_f32);
+    if (!done) switch (m->plan.scan_threads) {
     case 64: done = scan_reg_dispatch<64>(m, want_f32); break;
     case 256: done = scan_reg_dispatch<256>(m, want_f32); break;
     default: done = scan_reg_dispatch<kScanThreads>(m, want_f32); break;

@@ -48,6 +48,8 @@ FP64_CASES = {
     # more shells than the register-resident scan holds (16 per thread x 128 threads): the
     # general chunked scan
     "long_radial_2100x2x4_L3": lambda: W.random_small((2100, 2, 4), 3, seed=9, r0=1.0, r1=2.0),
+    # many moment columns (K_L = 2601): the recurrences take four adjacent columns per block
+    "many_moments_40x64x128_L50": lambda: W.presn(n_r=40, n_theta=64, n_phi=128, L=50, r_lo=1e7, r_hi=3e7),
 }
 
 
@@ -74,6 +76,8 @@ SPLIT_CASES = {
                                    ("bf16x3", "bf16x6")),
     "monopole_L0_8x16x32": (lambda: W.presn(n_r=8, n_theta=16, n_phi=32, L=0), ("bf16x3",)),
     "random_rough_6x32x64_L8": (lambda: W.random_small((6, 32, 64), 8, seed=8, r0=0.2, r1=1.0), ("bf16x6",)),
+    "many_moments_40x64x128_L50": (lambda: W.presn(n_r=40, n_theta=64, n_phi=128, L=50, r_lo=1e7, r_hi=3e7),
+                                   ("bf16x3",)),
     # more 128-row tiles than the projection's persistent grid has CTAs, the last tile ragged
     "multi_wave_200x100x32_L8": (lambda: W.presn(n_r=200, n_theta=100, n_phi=32, L=8), ("bf16x3", "bf16x6")),
     # tables too large for shared memory: the direct theta contraction and the per-row
