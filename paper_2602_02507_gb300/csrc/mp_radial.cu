@@ -602,11 +602,30 @@ static bool scan_reg_dispatch(mp_mesh *m, int want_f32)
     return true;
 }
 
+// Shared memory of the persistent theta contraction (table, two shell buffers, item
+// list, barriers); above 200 KB the per-order GEMM form runs instead.
+static size_t theta_pipe_smem(const mp_mesh *m, int *n_items_out = nullptr, int *jsh_out = nullptr)
+{
+    const int ldF = m->plan.ldF, L = m->L, P = m->P;
+    const size_t tab_bytes = (size_t)m->T * ldF * 4;
+    int n_items = 0;
+    for (int mm = 0; mm <= L; ++mm) n_items += (L + 2 - mm) / 2;
+    // lanes per item: eight when a row has enough float4 units to go round
+    const int nq = (m->n_t + 3) / 4;
+    const int jsh = nq >= 16 ? 3 : (nq >= 8 ? 2 : (nq >= 4 ? 1 : 0));
+    if (n_items_out) *n_items_out = n_items;
+    if (jsh_out) *jsh_out = jsh;
+    return tab_bytes + 2 * (size_t)P * ldF * 4 + (size_t)((n_items + 1) & ~1) * 4 + 3 * 8 + 16;
+}
+
 // Four columns per block when there are at least four such blocks per SM; 128 chunk
-// threads per column (512 per block), CH shells each.
+// threads per column (512 per block), CH shells each.  Not beside the persistent theta
+// contraction of the split path: its blocks leave room for the small one-column scan
+// blocks to start early, not for these (that early start is worth more than coalescing).
 static bool scan_q4_dispatch(mp_mesh *m, int want_f32)
 {
-    if (m->KL < 16 * m->num_sms) return false;
+    if (m->KL < 4 * m->num_sms) return false;
+    if (want_f32 && theta_pipe_smem(m) <= 200 * 1024) return false;
     const int ch = (m->n_r + 127) / 128;
     auto go = [&](auto kern) {
         launch_pdl(kern, dim3((m->KL + 3) / 4), dim3(512), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
@@ -649,12 +668,8 @@ cudaError_t launch_split_theta(mp_mesh *m)
     constexpr double kFourPi = 12.566370614359172954;
     const int ldF = m->plan.ldF, L = m->L, P = m->P;
     const uint32_t tab_bytes = (uint32_t)((size_t)m->T * ldF * 4);
-    int n_items = 0;
-    for (int mm = 0; mm <= L; ++mm) n_items += (L + 2 - mm) / 2;
-    // lanes per item: eight when a row has enough float4 units to go round
-    const int nq = (m->n_t + 3) / 4;
-    const int jsh = nq >= 16 ? 3 : (nq >= 8 ? 2 : (nq >= 4 ? 1 : 0));
-    const size_t smem = (size_t)tab_bytes + 2 * (size_t)P * ldF * 4 + (size_t)((n_items + 1) & ~1) * 4 + 3 * 8 + 16;
+    int n_items = 0, jsh = 0;
+    const size_t smem = theta_pipe_smem(m, &n_items, &jsh);
     cudaEvent_t ev;
     prof_begin(m, "split_theta_contract", &ev);
     if (smem <= 200 * 1024) {
