@@ -40,7 +40,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Poisson solves/s & Gcell*mode/s, BF16x3 vs FP64 GPU at <=1e-6 rel err in Phi"
-WORKLOAD = "presupernova core 512x128x256 cells, geometric r in [1e5,1e10] cm, l_max=16, seed 2"
+WORKLOADS = {
+    # the benchmarked configuration (default)
+    "presn": "presupernova core 512x128x256 cells, geometric r in [1e5,1e10] cm, l_max=16, seed 2",
+    # a larger one for measurement and profiling of the large-table kernels
+    "lognormal": "log-normal angular field 1024x256x512 cells, geometric r in [1e5,1e12] cm, l_max=32, seed 3",
+}
 SPLIT_PRECISION = "bf16x3"
 
 # DRAM bytes (read + write) per launch from one ncu capture of the same
@@ -65,6 +70,8 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=50)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU-baseline budget")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="presn",
+                   help="mesh and density (presn is the benchmarked configuration)")
     return p.parse_args()
 
 
@@ -184,7 +191,7 @@ def run_reference(args):
     from oracle import oracle as O
     from paper_2602_02507_gb300 import workloads as W
     oracle_build.build()
-    w = W.presn()
+    w = getattr(W, args.workload)()
     m = w.mesh
     tab = O.build_tables(m.r, m.theta, m.phi, m.L)
     for _ in range(args.warmup):
@@ -200,7 +207,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)", "cells": m.cells, "l_max": m.L},
+        "config": {"workload": WORKLOADS[args.workload], "precision": "fp64 (CPU oracle)", "cells": m.cells,
+                   "l_max": m.L},
         "gcell_mode_per_s": value * m.cells * m.KL / 1e9,
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": O.get_threads(), "kind": "oracle",
                          "sample": sample},
@@ -268,7 +276,7 @@ def run_ours(args):
     def max_over_ranks(x: float) -> float:
         return max_over_ranks_on(x, world, "cuda")
 
-    w = W.presn()
+    w = getattr(W, args.workload)()
     m = w.mesh
     cells, KL = m.cells, m.KL
     rows = m.shape[0] * m.shape[1]
@@ -425,7 +433,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = nbytes / (avg_ms * 1e-3) / 1e9
     traffic = None
-    rec = NCU_TRAFFIC.get(dom)
+    rec = NCU_TRAFFIC.get(dom) if args.workload == "presn" else None  # the record is for that workload
     if rec and rec[2] == source_hash(rec[1]):
         traffic = rec[0]
     kernels = {k: {"launches": v["launches"], "avg_us": 1e3 * v["total_ms"] / v["launches"],
@@ -436,9 +444,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": SPLIT_PRECISION, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": cells, "l_max": m.L, "moments": KL,
+            "config": {"workload": WORKLOADS[args.workload], "cells": cells, "l_max": m.L, "moments": KL,
                        "precision": SPLIT_PRECISION, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (rho 134 MB + Phi 134 MB per step)"},
+                       "l2": f"inputs larger than L2 (rho {8 * cells / 1e6:.0f} MB + Phi {8 * cells / 1e6:.0f} MB per step)"},
             "gcell_mode_per_s": value * cells * KL / 1e9,
             "fp64_gpu": {"solves_per_s": world / (ms64 * 1e-3), "ms_per_solve": ms64, "steps": k64,
                          "gcell_mode_per_s": world / (ms64 * 1e-3) * cells * KL / 1e9},
