@@ -54,11 +54,13 @@ __global__ void __launch_bounds__(256) k_gravity(const double *__restrict__ phi,
         }
         const double nr = -__ldcs(rho + c);
         if (S) {
-            __stcs(S + c, nr * g0);
-            __stcs(S + N + c, nr * g1);
-            __stcs(S + 2 * N + c, nr * g2);
-        }
-        if (E) {
+            const double s0 = nr * g0, s1 = nr * g1, s2 = nr * g2;
+            __stcs(S + c, s0);
+            __stcs(S + N + c, s1);
+            __stcs(S + 2 * N + c, s2);
+            // E = v^a S_a: the products are already there (12 float64 operations a cell, not 13)
+            if (E) __stcs(E + c, fma(__ldcs(v + 2 * N + c), s2, fma(__ldcs(v + N + c), s1, __ldcs(v + c) * s0)));
+        } else if (E) {
             const double vg = fma(__ldcs(v + 2 * N + c), g2, fma(__ldcs(v + N + c), g1, __ldcs(v + c) * g0));
             __stcs(E + c, nr * vg);
         }

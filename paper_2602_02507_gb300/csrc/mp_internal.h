@@ -113,6 +113,7 @@ struct mp_mesh {
     std::vector<int> h_ctheta, h_cphi;
     int4 *d_cwork = nullptr;
     int n_cwork = 0;
+    int n_cwork_pairs = 0;  // leading entries of d_cwork that the two-column kernel takes
     double *d_cweights = nullptr;
     uint8_t *d_tabB = nullptr;    // projection B operand, bf16 x 3 terms, canonical layout
     uint8_t *d_tabT = nullptr;    // synthesis B operand, bf16 x 3 terms, canonical layout

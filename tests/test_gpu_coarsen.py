@@ -23,6 +23,8 @@ MESHES = {
     "paper_3d_24_non_power_of_two": lambda: W.paper_mesh(24, 0.25, 3.68, 0, 3),
     "paper_3d_64": lambda: W.paper_mesh(64, 0.25, 3.68, 0, 3),
     "paper_2d_48": lambda: W.paper_mesh(48, 0.25, 3.68, 0, 2),
+    # 54 azimuthal cells (2 x 27): two columns a thread; odd polar count: whole-range polar blocks
+    "paper_3d_27_n_phi_54": lambda: W.paper_mesh(27, 0.25, 3.68, 0, 3),
     "offset_geometric_3d": lambda: W.Mesh(np.geomspace(1e5, 1e7, 41), np.linspace(0, np.pi, 21),
                                           np.linspace(0, 2 * np.pi, 41), 0, 1.0, "geo"),
     # 640 azimuthal cells (2^7 x 5): whole-ring blocks wider than one pass of the CTA
@@ -59,16 +61,18 @@ def test_factors_and_means_match_oracle(name):
     assert np.array_equal(got[untouched], f[untouched])
 
 
+@pytest.mark.parametrize("gap", [37, 38])
 @pytest.mark.parametrize("name", ["paper_3d_16", "paper_3d_24_non_power_of_two"])
-def test_several_fields_with_a_gap_between_them(name):
+def test_several_fields_with_a_gap_between_them(name, gap):
     # an odd gap leaves the fields 8-byte aligned only: the one-column paths (and, with
-    # 48 azimuthal cells, whole rings spanning two warp chunks)
+    # 48 azimuthal cells, whole rings spanning two warp chunks); an even one keeps every
+    # field 16-byte aligned: the four-column path on each
     import torch
     from oracle import coarsen as O
     m, mesh = _mesh(name)
     shape = (m.r.size - 1, m.theta.size - 1, m.phi.size - 1)
     n = int(np.prod(shape))
-    stride = n + 37
+    stride = n + gap
     rng = np.random.default_rng(9)
     buf = rng.normal(size=3 * stride)
     t = torch.from_numpy(buf.copy()).cuda()
