@@ -156,7 +156,8 @@ static void free_mesh_buffers(mp_mesh *m)
                     m->d_GR,  m->d_GI,   m->d_V,      m->d_A,     m->d_MR,     m->d_MI,    m->d_C,
                     m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_Ith32, m->d_Itc32, m->d_Itc0, m->d_C0, m->d_colsum,
                     m->d_tabB, m->d_tabT, m->d_Aop, m->d_G0, m->phi_own, m->h_rho[0], m->h_rho[1],
-                    m->h_phi[0], m->h_phi[1], m->d_err, m->d_gst, m->d_cwork, m->d_cweights};
+                    m->h_phi[0], m->h_phi[1], m->d_err, m->d_gst, m->d_cwork, m->d_cweights, m->d_cgroups,
+                    m->d_cchunks, m->d_cscratch, m->d_ccount};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &pe : m->prof_pending) {

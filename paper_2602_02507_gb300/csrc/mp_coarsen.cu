@@ -13,15 +13,23 @@
 //
 // The host turns the rule into a work list once per mesh: one entry per polar
 // block that is coarsened (p > 1 or q > 1); cells outside every block are not
-// touched.  One CTA per (entry, field).  Azimuthal blocks of a power of two up to
-// 128 cells (n_phi a multiple of 4): threads run along phi four columns at a time
-// (two 16-byte accesses), each sums its columns over the polar block with the
-// block's normalised polar weights (none for a single polar cell), and the block's
-// lanes add their sums, weighted by normalised azimuthal weights, by shuffles: about
-// 1.2 float64 operations a cell on the paper mesh, the float64 pipe of this part being
-// the bound before HBM.  Two columns (odd multiples of 2) or one column per thread
-// (odd n_phi, unaligned fields) otherwise; wider blocks: the whole CTA reduces each
-// one.  Every coarsened cell is read once and written once.  Float64 throughout.
+// touched.  Each cell's mean is the normalised polar weights (dmu_j / sum dmu, none
+// for a single polar cell) applied along theta, then the normalised azimuthal
+// weights along phi, so that a single-row block of two cells costs one float64
+// multiply and one multiply-add: the float64 pipe of this part (about 0.5 T
+// instructions/s), not HBM, bounds the kernel.  On 16-byte aligned fields (even
+// n_phi) one launch holds three kinds of CTA:
+//   * blocks of more than kStageRows rows: one CTA per chunk of kStageRows rows
+//     (partial polar sums to scratch; the CTA that finishes an entry's last chunk
+//     forms and writes the means), so that the whole-sphere block near the origin
+//     is not one long chain of loads on one SM;
+//   * wide blocks (a power of two above 64 cells, or the whole ring): one CTA each,
+//     reduced across the CTA;
+//   * the rest (power-of-two azimuthal blocks up to 64 cells): runs of consecutive
+//     entries of at most kStageRows rows, all their rows copied to shared memory by
+//     cp.async at once, two columns a thread, shuffles within each azimuthal block.
+// Otherwise one CTA per entry, one column a thread.  Every coarsened cell is read
+// once and written once.  Float64 throughout.
 #include <algorithm>
 #include <cmath>
 
@@ -34,66 +42,200 @@ namespace {
 
 constexpr int kCoarsenThreads = 256;
 constexpr int kCoarsenLevels = 7;  // azimuthal block sizes 1, 2, 4, ..., 64 have normalised weights
+constexpr int kStageRows = 8;      // rows a CTA stages at once (16 bytes a thread each)
+constexpr int kFieldBatch = 4;     // fields per launch on aligned fields (scratch and counters for each)
+
+struct CoarsenArgs {
+    double *f;
+    long long stride;
+    const int4 *work;      // entries: shell, first polar cell, polar size ct, azimuthal size cp
+    const int2 *groups;    // runs: first entry, number of entries
+    const int4 *chunks;    // chunks of many-row blocks: entry, chunk, first scratch row, counter
+    double *scratch;       // [field][scratch row][n_phi] polar sums of the chunks
+    int *counters;         // [field][many-row block] finished chunks
+    const double *dmu, *dph, *nph, *inv_mu, *nth;
+    int n_th_rows, n_t, n_p;
+    int e_wide_first;      // first entry taken one per CTA
+    int n_chunk_ctas, n_wide_ctas, n_big, n_scratch_rows;
+};
 
 // The block's mean is sum_j sum_k (dmu_j / sum dmu) (dphi_k / sum_{block} dphi) K_jk: the
-// normalised azimuthal weights nph[level][k] (block size 2^level) come from the host.
-// VEC = 2: 16-byte accesses (two columns a thread), VEC = 1: one column a thread.
-template <int VEC>
-__global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict__ f, long long stride,
-                                                             const int4 *__restrict__ work,
-                                                             const double *__restrict__ dmu,
-                                                             const double *__restrict__ dph,
-                                                             const double *__restrict__ nph,
-                                                             const double *__restrict__ inv_mu,
-                                                             const double *__restrict__ nth, int n_th_rows, int n_t,
-                                                             int n_p)
+// normalised polar weights nth[row][j] (row log2 of the polar block size, or the last row for
+// the whole polar range) and azimuthal weights nph[level][k] (block size 2^level) come from
+// the host.
+
+__device__ __forceinline__ void cp_async16(double2 *dst, const double *src)
 {
-    const int4 wk = work[blockIdx.x];  // shell, first polar cell, polar size, azimuthal size
-    const int j0 = wk.y, ct = wk.z, cp = wk.w;
-    double *base = f + (long long)blockIdx.y * stride + ((long long)wk.x * n_t + j0) * n_p;
-    const int lane = threadIdx.x & 31;
-    const bool pow2 = (cp & (cp - 1)) == 0;
-    const double inv = inv_mu[blockIdx.x];  // 1 / sum of dmu over the polar block (no divisions here:
-                                            // they are slow on the float64 pipe of this part)
-    if (VEC == 2 && pow2 && cp <= 64) {
-        // two adjacent columns per thread (16-byte accesses along phi): each sums its columns
-        // over the polar block with the block's normalised polar weights (none for a single
-        // polar cell); the cp / 2 lanes of an azimuthal block (aligned: 64 columns per warp, a
-        // multiple of cp) add their sums, weighted by the normalised azimuthal weights, by shuffles
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// The mean of one power-of-two azimuthal block (up to 64 cells) from the polar sums c0, c1 of a
+// thread's two columns k, k + 1: the cp / 2 lanes of the block (aligned: 64 columns per warp,
+// a multiple of cp) add their sums, weighted by the normalised azimuthal weights, by shuffles;
+// every cell of the block's ct rows takes it.  All lanes of the warp call this together.
+__device__ __forceinline__ void coarsen_finish(double *base, int ct, int cp, const double *__restrict__ nph, int n_p,
+                                               int k, bool in, double c0, double c1)
+{
+    double2 out = make_double2(c0, c1);
+    if (cp > 1) {
         const double *w_phi = nph + (size_t)(__ffs(cp) - 1) * n_p;
-        const double *w_th = nth + (size_t)((ct & (ct - 1)) == 0 ? __ffs(ct) - 1 : n_th_rows - 1) * n_t + j0;
-        for (int k0 = 0; k0 < n_p; k0 += 2 * (int)blockDim.x) {
-            const int k = k0 + 2 * (int)threadIdx.x;
-            const bool in = k < n_p;
+        double num = in ? fma(__ldg(w_phi + k + 1), c1, __ldg(w_phi + k) * c0) : 0.0;
+        for (int o = 1; o < cp / 2; o <<= 1) num += __shfl_xor_sync(0xFFFFFFFFu, num, o);
+        out = make_double2(num, num);
+    }
+    if (in)
+        for (int j = 0; j < ct; ++j) *reinterpret_cast<double2 *>(base + (long long)j * n_p + k) = out;
+}
+
+// A run of consecutive entries with power-of-two azimuthal blocks up to 64 cells and at most
+// kStageRows rows in all (16-byte aligned fields).  Each thread owns two adjacent columns
+// along phi and copies its
+// 16 bytes of every row of the run into its own shared-memory slots (cp.async: all the
+// rows' loads in flight together, no registers held for them), then sums its columns over
+// each block's rows with the normalised polar weights (none for a single polar cell).
+__device__ __forceinline__ void coarsen_run(double *fld, const int4 *__restrict__ work, int2 g,
+                                            const double *__restrict__ nph, const double *__restrict__ nth,
+                                            int n_th_rows, int n_t, int n_p, double2 *stage)
+{
+    const int nthr = (int)blockDim.x, tid = (int)threadIdx.x;
+    for (int k0 = 0; k0 < n_p; k0 += 2 * nthr) {
+        const int k = k0 + 2 * tid;
+        const bool in = k < n_p;
+        int row = 0;
+        for (int q = 0; q < g.y; ++q) {
+            const int4 wk = work[g.x + q];
+            const double *base = fld + ((long long)wk.x * n_t + wk.y) * n_p + k;
+            if (in)
+                for (int j = 0; j < wk.z; ++j) cp_async16(stage + (row + j) * nthr + tid, base + (long long)j * n_p);
+            row += wk.z;
+        }
+        cp_async_wait_all();
+        row = 0;
+        for (int q = 0; q < g.y; ++q) {
+            const int4 wk = work[g.x + q];
+            const int j0 = wk.y, ct = wk.z;
             double c0 = 0.0, c1 = 0.0;
             if (in) {
                 if (ct == 1) {
-                    const double2 v = *reinterpret_cast<const double2 *>(base + k);
+                    const double2 v = stage[row * nthr + tid];
                     c0 = v.x;
                     c1 = v.y;
                 } else {
-#pragma unroll 4
+                    const double *w_th = nth + (size_t)((ct & (ct - 1)) == 0 ? __ffs(ct) - 1 : n_th_rows - 1) * n_t + j0;
                     for (int j = 0; j < ct; ++j) {
-                        const double2 v = *reinterpret_cast<const double2 *>(base + (long long)j * n_p + k);
+                        const double2 v = stage[(row + j) * nthr + tid];
                         const double w = __ldg(w_th + j);
                         c0 = fma(w, v.x, c0);
                         c1 = fma(w, v.y, c1);
                     }
                 }
             }
-            double2 out;
-            if (cp == 1) {
-                out = make_double2(c0, c1);
-            } else {
-                double num = in ? fma(__ldg(w_phi + k + 1), c1, __ldg(w_phi + k) * c0) : 0.0;
-                for (int o = 1; o < cp / 2; o <<= 1) num += __shfl_xor_sync(0xFFFFFFFFu, num, o);
-                out = make_double2(num, num);
-            }
-            if (in)
-                for (int j = 0; j < ct; ++j) *reinterpret_cast<double2 *>(base + (long long)j * n_p + k) = out;
+            coarsen_finish(fld + ((long long)wk.x * n_t + j0) * n_p, ct, wk.w, nph, n_p, k, in, c0, c1);
+            row += ct;
         }
-        return;
     }
+}
+
+// Polar blocks of more than kStageRows rows (16-byte aligned fields): one CTA per chunk of
+// kStageRows rows, so that such a block is not one long chain of loads on one SM.  Chunk
+// d = (entry, chunk, first scratch row of the entry, counter) writes the polar sums of its
+// rows per column (normalised polar weights) to scratch; the CTA that finishes an entry's
+// last chunk (a counter per entry and field, reset by that CTA) adds the chunks' sums in
+// chunk order, forms each azimuthal block's mean sum dphi_k S_k / sum dphi_k (any block
+// width) and writes it to every cell of the block.  No CTA waits for another.
+__device__ __forceinline__ void coarsen_chunk(double *fld, const CoarsenArgs &a, int4 d, double *sm)
+{
+    const int nthr = (int)blockDim.x, tid = (int)threadIdx.x, n_t = a.n_t, n_p = a.n_p;
+    const int4 wk = a.work[d.x];
+    const int j0 = wk.y, ct = wk.z, cp = wk.w;
+    const int n_ch = (ct + kStageRows - 1) / kStageRows, r0 = d.y * kStageRows, nr = min(kStageRows, ct - r0);
+    double *base = fld + ((long long)wk.x * n_t + j0) * n_p;
+    const double *w_th = a.nth + (size_t)((ct & (ct - 1)) == 0 ? __ffs(ct) - 1 : a.n_th_rows - 1) * n_t + j0;
+    double *part = a.scratch + ((long long)blockIdx.y * a.n_scratch_rows + d.z) * n_p;
+    for (int k = 2 * tid; k < n_p; k += 2 * nthr) {
+        double c0 = 0.0, c1 = 0.0;
+#pragma unroll
+        for (int r = 0; r < kStageRows; ++r)
+            if (r < nr) {
+                const double2 v = *reinterpret_cast<const double2 *>(base + (long long)(r0 + r) * n_p + k);
+                const double w = __ldg(w_th + r0 + r);
+                c0 = fma(w, v.x, c0);
+                c1 = fma(w, v.y, c1);
+            }
+        __stcg(reinterpret_cast<double2 *>(part + (long long)d.y * n_p + k), make_double2(c0, c1));
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int s_last;
+    int *cnt = a.counters + blockIdx.y * a.n_big + d.w;
+    if (tid == 0) s_last = atomicAdd(cnt, 1) == n_ch - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double *sS = sm, *sM = sm + n_p;  // column sums, block means
+    for (int k = tid; k < n_p; k += nthr) {
+        double acc = 0.0;
+        for (int c = 0; c < n_ch; ++c) acc += __ldcg(part + (long long)c * n_p + k);
+        sS[k] = acc;
+    }
+    __syncthreads();
+    const int lane = tid & 31, nkb = n_p / cp;
+    for (int b = tid >> 5; b < nkb; b += nthr >> 5) {
+        double num = 0.0, den = 0.0;
+        for (int k = b * cp + lane; k < (b + 1) * cp; k += 32) {
+            const double dp = __ldg(a.dph + k);
+            num = fma(dp, sS[k], num);
+            den += dp;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xFFFFFFFFu, num, o);
+            den += __shfl_xor_sync(0xFFFFFFFFu, den, o);
+        }
+        if (lane == 0) sM[b] = num / den;  // one division per block
+    }
+    __syncthreads();
+    for (int k = 2 * tid; k < n_p; k += 2 * nthr) {
+        const double2 out = make_double2(sM[k / cp], sM[(k + 1) / cp]);
+        for (int j = 0; j < ct; ++j) *reinterpret_cast<double2 *>(base + (long long)j * n_p + k) = out;
+    }
+    if (tid == 0) *cnt = 0;  // ready for the next launch
+}
+
+// VEC = 2 (16-byte aligned fields, even n_phi): the CTAs take, in this order, one chunk of a
+// block of many rows each, one entry of a wide block each (a power of two above 64 cells, or
+// the whole ring) and one run of groups[] each.  VEC = 1: one entry per CTA, all of them.
+template <int VEC>
+__global__ void __launch_bounds__(kCoarsenThreads, 6) k_coarsen(const CoarsenArgs a)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    double *fld = a.f + (long long)blockIdx.y * a.stride;
+    const int n_t = a.n_t, n_p = a.n_p;
+    int x = (int)blockIdx.x;
+    if (VEC == 2) {
+        if (x < a.n_chunk_ctas) {
+            coarsen_chunk(fld, a, a.chunks[x], reinterpret_cast<double *>(dsm));
+            return;
+        }
+        x -= a.n_chunk_ctas;
+        if (x >= a.n_wide_ctas) {
+            coarsen_run(fld, a.work, a.groups[x - a.n_wide_ctas], a.nph, a.nth, a.n_th_rows, n_t, n_p,
+                        reinterpret_cast<double2 *>(dsm));
+            return;
+        }
+    }
+    const double *__restrict__ dmu = a.dmu, *__restrict__ dph = a.dph, *__restrict__ nph = a.nph;
+    const int e = a.e_wide_first + x;
+    const int4 wk = a.work[e];  // shell, first polar cell, polar size, azimuthal size
+    const int j0 = wk.y, ct = wk.z, cp = wk.w;
+    double *base = fld + ((long long)wk.x * n_t + j0) * n_p;
+    const int lane = threadIdx.x & 31;
+    const bool pow2 = (cp & (cp - 1)) == 0;
+    const double inv = a.inv_mu[e];  // 1 / sum of dmu over the polar block (no divisions here:
+                                     // they are slow on the float64 pipe of this part)
     if (VEC == 1 && pow2 && cp <= 32) {
         // one column per thread (odd n_phi or unaligned fields)
         const double *w_phi = nph + (size_t)(__ffs(cp) - 1) * n_p;
@@ -118,7 +260,7 @@ __global__ void __launch_bounds__(kCoarsenThreads) k_coarsen(double *__restrict_
     // reduces its chunk of 32 V columns, and one thread per azimuthal block adds its chunks
     // in order (a chunk never straddles two blocks: cp is a multiple of 32 V, or the block
     // is the whole ring)
-    extern __shared__ double chunk[];  // per chunk of 32 V columns: num, den; then per block: the mean
+    double *chunk = reinterpret_cast<double *>(dsm);  // per chunk of 32 V columns: num, den; then per block: the mean
     constexpr int V = VEC;
     const int per_warp = 32 * V, warp = threadIdx.x >> 5;
     const int n_chunks = (n_p + per_warp - 1) / per_warp;
@@ -224,10 +366,39 @@ cudaError_t coarsen_prepare(mp_mesh *m)
             if (ct > 1 || cp > 1) work.push_back(make_int4(i, j0, ct, cp));
         }
     }
-    // the polar blocks with the most rows first: their CTAs run longest (a chain of row loads)
-    // and so start while the many short ones stream past them
-    std::stable_sort(work.begin(), work.end(), [](const int4 &a, const int4 &b) { return a.z > b.z; });
+    // order of the entries: power-of-two azimuthal blocks up to 64 cells of at most kStageRows
+    // rows (staged in runs on aligned fields), other blocks of at most kStageRows rows (one
+    // CTA each), blocks of more rows (chunks of kStageRows rows); each part in mesh order
+    const auto is_run = [](const int4 &e) { return e.z <= kStageRows && (e.w & (e.w - 1)) == 0 && e.w <= 64; };
+    const auto is_short = [](const int4 &e) { return e.z <= kStageRows; };
+    std::stable_partition(work.begin(), work.end(), is_short);
+    std::stable_partition(work.begin(), work.end(), is_run);
     m->n_cwork = (int)work.size();
+    m->n_cwork_fast = (int)std::count_if(work.begin(), work.end(), is_run);
+    m->n_cwork_wide = (int)std::count_if(work.begin(), work.end(), is_short) - m->n_cwork_fast;
+    std::vector<int2> groups;  // runs of consecutive entries of at most kStageRows rows in all
+    int open_rows = kStageRows + 1;  // rows in the last run (above kStageRows: none open)
+    for (int e = 0; e < m->n_cwork_fast; ++e) {
+        const int ct = work[e].z;
+        if (open_rows + ct > kStageRows) {
+            groups.push_back(make_int2(e, 1));
+            open_rows = ct;
+        } else {
+            ++groups.back().y;
+            open_rows += ct;
+        }
+    }
+    std::vector<int4> chunks;  // entry, chunk, first scratch row, counter
+    m->n_cbig = 0;
+    m->n_cscratch_rows = 0;
+    for (int e = m->n_cwork_fast + m->n_cwork_wide; e < m->n_cwork; ++e) {
+        const int n_ch = (work[e].z + kStageRows - 1) / kStageRows;
+        for (int c = 0; c < n_ch; ++c) chunks.push_back(make_int4(e, c, m->n_cscratch_rows, m->n_cbig));
+        m->n_cscratch_rows += n_ch;
+        ++m->n_cbig;
+    }
+    m->n_cchunks = (int)chunks.size();
+    m->n_cgroups = (int)groups.size();
     std::vector<double> inv_mu(std::max<size_t>(1, work.size()), 0.0);
     for (size_t e = 0; e < work.size(); ++e) {
         double sum = 0.0;
@@ -271,6 +442,28 @@ cudaError_t coarsen_prepare(mp_mesh *m)
         e = cudaMemcpy(m->d_cwork, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
     }
+    e = cudaMalloc(reinterpret_cast<void **>(&m->d_cgroups), std::max<size_t>(1, groups.size()) * sizeof(int2));
+    if (e != cudaSuccess) return e;
+    m->device_bytes += std::max<size_t>(1, groups.size()) * sizeof(int2);
+    if (!groups.empty()) {
+        e = cudaMemcpy(m->d_cgroups, groups.data(), groups.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    if (m->n_cbig > 0) {
+        e = cudaMalloc(reinterpret_cast<void **>(&m->d_cchunks), chunks.size() * sizeof(int4));
+        if (e != cudaSuccess) return e;
+        e = cudaMalloc(reinterpret_cast<void **>(&m->d_cscratch),
+                       (size_t)kFieldBatch * m->n_cscratch_rows * n_p * sizeof(double));
+        if (e != cudaSuccess) return e;
+        e = cudaMalloc(reinterpret_cast<void **>(&m->d_ccount), (size_t)kFieldBatch * m->n_cbig * sizeof(int));
+        if (e != cudaSuccess) return e;
+        m->device_bytes += chunks.size() * sizeof(int4) + (size_t)kFieldBatch * m->n_cscratch_rows * n_p * sizeof(double) +
+                           (size_t)kFieldBatch * m->n_cbig * sizeof(int);
+        e = cudaMemset(m->d_ccount, 0, (size_t)kFieldBatch * m->n_cbig * sizeof(int));
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(m->d_cchunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
     return cudaMemcpy(m->d_cweights, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
@@ -279,27 +472,58 @@ cudaError_t launch_coarsen(mp_mesh *m, double *fields, int n_fields, long long s
     if (m->n_cwork == 0 || n_fields == 0) return cudaSuccess;
     cudaEvent_t ev;
     prof_begin(m, "coarsen_blocks", &ev);
-    // 16-byte accesses need even n_phi and 16-byte aligned fields; four columns a thread also
-    // need n_phi a multiple of 4
-    const bool al = (m->n_p % 2 == 0) && (reinterpret_cast<uintptr_t>(fields) % 16 == 0) && (stride % 2 == 0);
-    const int vec = !al ? 1 : 2;
-    // as many threads as one pass along a ring takes at the widest access (at most 256)
+    // 16-byte accesses need even n_phi and 16-byte aligned fields
+    const int vec = (m->n_p % 2 == 0) && (reinterpret_cast<uintptr_t>(fields) % 16 == 0) && (stride % 2 == 0) ? 2 : 1;
+    // as many threads as one pass along a ring takes (at most 256)
     const int threads = std::min(kCoarsenThreads, std::max(32, 32 * ((m->n_p + 32 * vec - 1) / (32 * vec))));
-    // wide blocks keep per-chunk sums and per-block means in dynamic shared memory
-    const int per_warp = vec >= 2 ? 64 : 32;
+    // wide blocks keep per-chunk sums and per-block means in dynamic shared memory; runs, the
+    // staged rows; the last chunk of a many-row block, column sums and block means
+    const int per_warp = 32 * vec;
     const int n_chunks = (m->n_p + per_warp - 1) / per_warp;
-    const size_t smem = (size_t)3 * n_chunks * sizeof(double);  // blocks here span whole chunks
+    size_t smem = (size_t)3 * n_chunks * sizeof(double);
+    if (vec == 2) smem = std::max({smem, (size_t)kStageRows * threads * 16, (size_t)2 * m->n_p * sizeof(double)});
+    if (smem > 48 * 1024) {
+        const cudaError_t e = vec == 2 ? cudaFuncSetAttribute(k_coarsen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                                       : cudaFuncSetAttribute(k_coarsen<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     const double *w = m->d_cweights;
     const size_t off_inv = (size_t)m->n_t + (size_t)m->n_p * (1 + kCoarsenLevels);
-    const dim3 grid((unsigned)m->n_cwork, (unsigned)n_fields);
-    if (vec == 2)
-        k_coarsen<2><<<grid, threads, smem, m->stream>>>(fields, stride, m->d_cwork, w, w + m->n_t, w + m->n_t + m->n_p,
-                                                         w + off_inv, w + off_inv + std::max(1, m->n_cwork),
-                                                         coarsen_theta_rows(m->n_t), m->n_t, m->n_p);
-    else
-        k_coarsen<1><<<grid, threads, smem, m->stream>>>(fields, stride, m->d_cwork, w, w + m->n_t, w + m->n_t + m->n_p,
-                                                         w + off_inv, w + off_inv + std::max(1, m->n_cwork),
-                                                         coarsen_theta_rows(m->n_t), m->n_t, m->n_p);
+    CoarsenArgs a;
+    a.f = fields;
+    a.stride = stride;
+    a.work = m->d_cwork;
+    a.groups = m->d_cgroups;
+    a.chunks = m->d_cchunks;
+    a.scratch = m->d_cscratch;
+    a.counters = m->d_ccount;
+    a.dmu = w;
+    a.dph = w + m->n_t;
+    a.nph = w + m->n_t + m->n_p;
+    a.inv_mu = w + off_inv;
+    a.nth = w + off_inv + std::max(1, m->n_cwork);
+    a.n_th_rows = coarsen_theta_rows(m->n_t);
+    a.n_t = m->n_t;
+    a.n_p = m->n_p;
+    a.n_big = m->n_cbig;
+    a.n_scratch_rows = m->n_cscratch_rows;
+    if (vec == 2) {
+        // chunks of many-row blocks, then wide blocks one per CTA, then runs; kFieldBatch fields
+        // a launch (the scratch and counters are per field of a launch)
+        a.e_wide_first = m->n_cwork_fast;
+        a.n_chunk_ctas = m->n_cchunks;
+        a.n_wide_ctas = m->n_cwork_wide;
+        const unsigned gx = (unsigned)(m->n_cchunks + m->n_cwork_wide + m->n_cgroups);
+        for (int f0 = 0; f0 < n_fields; f0 += kFieldBatch) {
+            a.f = fields + (long long)f0 * stride;
+            k_coarsen<2><<<dim3(gx, (unsigned)std::min(kFieldBatch, n_fields - f0)), threads, smem, m->stream>>>(a);
+        }
+    } else {
+        a.e_wide_first = 0;
+        a.n_chunk_ctas = 0;
+        a.n_wide_ctas = m->n_cwork;
+        k_coarsen<1><<<dim3((unsigned)m->n_cwork, (unsigned)n_fields), threads, smem, m->stream>>>(a);
+    }
     prof_end(m, "coarsen_blocks", ev);
     return cudaGetLastError();
 }

@@ -113,7 +113,14 @@ struct mp_mesh {
     std::vector<int> h_ctheta, h_cphi;
     int4 *d_cwork = nullptr;
     int n_cwork = 0;
-    int n_cwork_pairs = 0;  // leading entries of d_cwork that the two-column kernel takes
+    int n_cwork_fast = 0;   // leading entries of d_cwork staged in runs (short blocks of up to 64 cells)
+    int n_cwork_wide = 0;   // then short blocks taken one per CTA; then blocks of many rows
+    int2 *d_cgroups = nullptr;  // runs: first entry, count
+    int n_cgroups = 0;
+    int4 *d_cchunks = nullptr;  // chunks of many-row blocks: entry, chunk, first scratch row, counter
+    int n_cchunks = 0, n_cbig = 0, n_cscratch_rows = 0;
+    double *d_cscratch = nullptr;  // per field of a launch: polar sums of the chunks
+    int *d_ccount = nullptr;       // per field of a launch and many-row block: finished chunks
     double *d_cweights = nullptr;
     uint8_t *d_tabB = nullptr;    // projection B operand, bf16 x 3 terms, canonical layout
     uint8_t *d_tabT = nullptr;    // synthesis B operand, bf16 x 3 terms, canonical layout

@@ -53,12 +53,18 @@ def test_factors_and_means_match_oracle(name):
         f = rng.normal(size=shape) * 10.0 + 3.0
         t = torch.from_numpy(f.reshape(-1).copy()).cuda()
         mesh.coarsen(t)
+        # a second field through the same mesh: the per-block state of the first call is reset
+        f2 = rng.normal(size=shape) - 1.0
+        t2 = torch.from_numpy(f2.reshape(-1).copy()).cuda()
+        mesh.coarsen(t2)
         mesh.synchronize()
         got = t.cpu().numpy().reshape(shape)
-    ref = O.coarsen(f, m.r, m.theta, m.phi)
-    assert np.all(np.abs(got - ref) <= 1e-13 * np.abs(ref) + 1e-13), float(np.abs(got - ref).max())
+        got2 = t2.cpu().numpy().reshape(shape)
     untouched = (oct_[:, None] == 1) & (ocp == 1)
-    assert np.array_equal(got[untouched], f[untouched])
+    for x, g in ((f, got), (f2, got2)):
+        ref = O.coarsen(x, m.r, m.theta, m.phi)
+        assert np.all(np.abs(g - ref) <= 1e-13 * np.abs(ref) + 1e-13), float(np.abs(g - ref).max())
+        assert np.array_equal(g[untouched], x[untouched])
 
 
 @pytest.mark.parametrize("gap", [37, 38])
@@ -66,7 +72,7 @@ def test_factors_and_means_match_oracle(name):
 def test_several_fields_with_a_gap_between_them(name, gap):
     # an odd gap leaves the fields 8-byte aligned only: the one-column paths (and, with
     # 48 azimuthal cells, whole rings spanning two warp chunks); an even one keeps every
-    # field 16-byte aligned: the four-column path on each
+    # field 16-byte aligned: the staged two-column paths on each, six fields in two launches
     import torch
     from oracle import coarsen as O
     m, mesh = _mesh(name)
@@ -74,14 +80,14 @@ def test_several_fields_with_a_gap_between_them(name, gap):
     n = int(np.prod(shape))
     stride = n + gap
     rng = np.random.default_rng(9)
-    buf = rng.normal(size=3 * stride)
+    buf = rng.normal(size=6 * stride)
     t = torch.from_numpy(buf.copy()).cuda()
     with mesh:
-        mesh.coarsen(t, n_fields=3, field_stride=stride)
+        mesh.coarsen(t, n_fields=6, field_stride=stride)
         mesh.coarsen(t, n_fields=0)  # nothing to do
         mesh.synchronize()
     got = t.cpu().numpy()
-    for fi in range(3):
+    for fi in range(6):
         ref = O.coarsen(buf[fi * stride:fi * stride + n].reshape(shape), m.r, m.theta, m.phi)
         g = got[fi * stride:fi * stride + n].reshape(shape)
         assert np.all(np.abs(g - ref) <= 1e-13 * np.abs(ref) + 1e-13)
