@@ -93,10 +93,10 @@ __device__ __forceinline__ void coarsen_finish(double *base, int ct, int cp, con
 
 // A run of consecutive entries with power-of-two azimuthal blocks up to 64 cells and at most
 // kStageRows rows in all (16-byte aligned fields).  Each thread owns two adjacent columns
-// along phi and copies its
-// 16 bytes of every row of the run into its own shared-memory slots (cp.async: all the
-// rows' loads in flight together, no registers held for them), then sums its columns over
-// each block's rows with the normalised polar weights (none for a single polar cell).
+// along phi and copies its 16 bytes of every row of the run into its own shared-memory
+// slots (cp.async: all the rows' loads in flight together, no registers held for them),
+// then sums its columns over each block's rows with the normalised polar weights (none for
+// a single polar cell).
 __device__ __forceinline__ void coarsen_run(double *fld, const int4 *__restrict__ work, int2 g,
                                             const double *__restrict__ nph, const double *__restrict__ nth,
                                             int n_th_rows, int n_t, int n_p, double2 *stage)
