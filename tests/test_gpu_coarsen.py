@@ -30,6 +30,9 @@ MESHES = {
     # 640 azimuthal cells (2^7 x 5): whole-ring blocks wider than one pass of the CTA
     "wide_rings_6x8x640": lambda: W.Mesh(np.linspace(0.0, 1.0, 7), np.linspace(0, np.pi, 9),
                                          np.linspace(0, 2 * np.pi, 641), 0, 1.0, "wide"),
+    # a 16-row whole-ring block at the first shell: chunks of rows wider than one pass of the CTA
+    "wide_rings_6x16x640_many_rows": lambda: W.Mesh(np.linspace(0.0, 1.0, 7), np.linspace(0, np.pi, 17),
+                                                    np.linspace(0, 2 * np.pi, 641), 0, 1.0, "wide16"),
 }
 
 
