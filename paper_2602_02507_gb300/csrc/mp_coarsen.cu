@@ -64,13 +64,11 @@ struct CoarsenArgs {
 // the whole polar range) and azimuthal weights nph[level][k] (block size 2^level) come from
 // the host.
 
-__device__ __forceinline__ void cp_async16(double2 *dst, const double *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
+__device__ __forceinline__ void cp_async16(double2 *dst, const double *src) { cp_async16_zfill(smem_u32(dst), src, 16); }
 __device__ __forceinline__ void cp_async_wait_all()
 {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    cp_async_commit();
+    cp_async_wait<0>();
 }
 
 // The mean of one power-of-two azimuthal block (up to 64 cells) from the polar sums c0, c1 of a
