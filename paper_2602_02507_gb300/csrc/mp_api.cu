@@ -287,7 +287,24 @@ static mp_status plan_split(mp_mesh *m)
         const int nq = (m->n_t + 3) / 4;
         pl.ldF = 4 * ((nq % 2 == 0) ? nq + 1 : nq + 2);
     }
-    pl.NC = std::min(256, round_up(m->n_p, 16));
+    {
+        // synthesis column chunk NC (<= 256 accumulator columns): the CTAs take (tile, chunk)
+        // units round-robin, so the last wave lasts one chunk; take the NC whose waves x
+        // (NC + a per-unit cost of about 32 columns) is least (ties: the wider chunk)
+        const long long n_tiles = (m->R + 127) / 128;
+        const int nc_max = std::min(256, round_up(m->n_p, 16));
+        long long best = -1;
+        for (int nc = nc_max; nc >= 64; nc /= 2) {
+            if (nc % 16) break;
+            const long long units = n_tiles * ((m->n_p + nc - 1) / nc);
+            const long long cost = (units + m->num_sms - 1) / m->num_sms * (nc + 32);
+            if (best < 0 || cost < best) {
+                best = cost;
+                pl.NC = nc;
+            }
+        }
+        if (best < 0) pl.NC = nc_max;
+    }
     pl.n_nc = (m->n_p + pl.NC - 1) / pl.NC;
     pl.proj_ctas = m->num_sms;
     pl.synth_ctas = m->num_sms;

@@ -802,6 +802,10 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
     const int Kpad = prm.Kpad, NC = prm.NC;
     const int nkk = Kpad / 16;
     const int n_chunks = prm.n_nc * nkk;
+    // work units (tile, column chunk nc), dealt out round-robin: a tile's chunks may go to
+    // different CTAs, each loading the tile's A operand, so that the last wave is a chunk
+    // rather than a whole tile
+    const int n_units = prm.n_tiles * prm.n_nc;
     const int b_slots = prm.b_resident ? n_chunks : NS_B;
     const uint32_t a_stage = prm.a_bytes + 1024;  // A operand terms + the tile's 128 m = 0 (hi, lo) pairs
     uint8_t *stg = smem;                                           // [16 warps][NSTG][4096]
@@ -852,7 +856,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
         // ---------------- producer: A tiles (+ m = 0 column) and table chunks
         if (lane == 0) {
             bool ok = true;
-            if (prm.b_resident && blockIdx.x < prm.n_tiles) {
+            if (prm.b_resident && blockIdx.x < n_units) {
                 // the whole table once; b_full[0] completes when every chunk has landed
                 mbar_arrive_expect_tx(smem_u32(&b_full[0]), (uint32_t)n_chunks * prm.bchunk);
                 for (int c = 0; c < n_chunks; ++c)
@@ -861,7 +865,8 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
             }
             pdl_wait();
             Ring ra, rb;
-            for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ra.next(NS_A)) {
+            for (int unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x, ra.next(NS_A)) {
+                const int tile = unit / prm.n_nc, nc = unit - tile * prm.n_nc;
                 ok = mbar_wait(smem_u32(&a_empty[ra.idx]), ra.phase ^ 1, abort_flag, prm.err);
                 if (!ok) break;
                 const uint32_t fb = smem_u32(&a_full[ra.idx]);
@@ -870,7 +875,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                 bulk_load(smem_u32(dst), prm.Aop + (size_t)tile * prm.a_bytes, prm.a_bytes, fb);
                 bulk_load(smem_u32(dst + prm.a_bytes), prm.G0 + (size_t)tile * 256, 1024, fb);
                 if (!prm.b_resident) {
-                    for (int c = 0; c < n_chunks && ok; ++c, rb.next(NS_B)) {
+                    for (int c = nc * nkk; c < (nc + 1) * nkk && ok; ++c, rb.next(NS_B)) {
                         ok = mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err);
                         if (!ok) break;
                         mbar_arrive_expect_tx(smem_u32(&b_full[rb.idx]), prm.bchunk);
@@ -895,13 +900,14 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
             Ring ra, rb;
             uint32_t u = 0;
             bool ok = true;
-            if (prm.b_resident && blockIdx.x < prm.n_tiles) ok = mbar_wait(smem_u32(&b_full[0]), 0, abort_flag, prm.err);
-            for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ra.next(NS_A)) {
+            if (prm.b_resident && blockIdx.x < n_units) ok = mbar_wait(smem_u32(&b_full[0]), 0, abort_flag, prm.err);
+            for (int unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x, ra.next(NS_A)) {
+                const int nc = unit % prm.n_nc;
                 ok = mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t a_base0 = smem_u32(sA + (size_t)ra.idx * a_stage);
-                for (int nc = 0; nc < prm.n_nc && ok; ++nc, ++u) {
+                {
                     const int buf = u & 1;
                     ok = mbar_wait(smem_u32(&acc_empty[buf]), ((u >> 1) & 1) ^ 1, abort_flag, prm.err);
                     if (!ok) break;
@@ -931,6 +937,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                     }
                     if (!ok) break;
                     umma_commit(smem_u32(&acc_full[buf]));
+                    ++u;
                 }
                 if (!ok) break;
                 umma_commit(smem_u32(&a_empty[ra.idx]));
@@ -953,7 +960,8 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
         int cs = 0;  // staging box of this warp in use
         bool ok = true;
         const int nmine = (NC / 16 - quarter + 3) / 4;  // chunks quarter, quarter + 4, ...
-        for (int tile = blockIdx.x; tile < prm.n_tiles && ok; tile += gridDim.x, ra.next(NS_A)) {
+        for (int unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x, ra.next(NS_A)) {
+            const int tile = unit / prm.n_nc, nc = unit - tile * prm.n_nc;
             const int rot = nmine > 0 ? rotated_chunk(0, tile, nmine) : 0;
             ok = warp_all(mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err));
             if (!ok) break;
@@ -962,7 +970,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
             if (lane == 0) mbar_arrive(smem_u32(&a_empty[ra.idx]));
             const long long box_row = (long long)tile * kBM + qd * 32;
             const bool box_valid = box_row < prm.R;
-            for (int nc = 0; nc < prm.n_nc && ok; ++nc, ++u) {
+            {
                 const int buf = u & 1;
                 ok = warp_all(mbar_wait(smem_u32(&acc_full[buf]), (u >> 1) & 1, abort_flag, prm.err));
                 if (!ok) break;
@@ -1001,6 +1009,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+                ++u;
             }
         }
         if (lane == 0) bulk_wait_all();
@@ -1323,7 +1332,7 @@ cudaError_t launch_split_synth(mp_mesh *m, double *phi)
     prm.b_resident = pl.b_resident;
     prm.a_bytes = (uint32_t)(pl.a_terms * kBM * pl.Kpad * 2);
     prm.bchunk = (uint32_t)(3 * pl.NC * 32);
-    const int grid = std::min(n_tiles, pl.synth_ctas);
+    const int grid = std::min(n_tiles * pl.n_nc, pl.synth_ctas);  // work units: (tile, column chunk)
     prof_begin(m, "split_synth_tc", &ev);
     if (pl.a_terms == 2)
         launch_pdl(k_synth_tc<2, 3>, dim3(grid), dim3(synth::THREADS), pl.synth_smem, m->stream, m->tm_phi, prm);
