@@ -54,7 +54,7 @@ SPLIT_PRECISION = "bf16x3"
 #               source file of the kernel, sha1 of that file and the shared headers at
 #               capture time); an entry whose sources changed since is ignored
 NCU_TRAFFIC = {
-    "split_phi_project_tc": (134318592 + 3093760, "mp_split.cu", "ebf3943dbb166e97f68668df7c963cf5e4548001"),
+    "split_phi_project_tc": (134322944 + 3294976, "mp_split.cu", "0daff66ddc57a6367dfeaddb11960824e8dfdc09"),
 }
 KERNEL_HEADERS = ("ptx.cuh", "mp_internal.h", "mp_errors.h")
 
