@@ -289,21 +289,26 @@ static mp_status plan_split(mp_mesh *m)
     }
     {
         // synthesis column chunk NC (<= 256 accumulator columns): the CTAs take (tile, chunk)
-        // units round-robin, so the last wave lasts one chunk; take the NC whose waves x
-        // (NC + a per-unit cost of about 32 columns) is least (ties: the wider chunk)
+        // units round-robin.  Take the widest NC in {256, 128, 64} that still gives every CTA
+        // about 12 units or more (the last wave then costs at most about a twelfth), else 64:
+        // wide chunks fetch a tile's A operand fewer times, narrow ones balance the CTAs.
+        // Measured on GB300: 512 x 128 x 256 cells at l_max = 16 (512 tiles) ran the synthesis
+        // in 27.1 / 28.6 / 28.9 us at NC = 64 / 128 / 256; 1024 x 256 x 512 cells at
+        // l_max = 32 (2048 tiles) in 262 / 208 / 173 us.
         const long long n_tiles = (m->R + 127) / 128;
         const int nc_max = std::min(256, round_up(m->n_p, 16));
-        long long best = -1;
-        for (int nc = nc_max; nc >= 64; nc /= 2) {
-            if (nc % 16) break;
-            const long long units = n_tiles * ((m->n_p + nc - 1) / nc);
-            const long long cost = (units + m->num_sms - 1) / m->num_sms * (nc + 32);
-            if (best < 0 || cost < best) {
-                best = cost;
-                pl.NC = nc;
+        pl.NC = nc_max;
+        if (nc_max >= 64) {
+            pl.NC = 64;
+            for (int nc = 256; nc >= 128; nc /= 2) {
+                if (nc > nc_max) continue;
+                const long long units = n_tiles * ((m->n_p + nc - 1) / nc);
+                if (units >= 12LL * m->num_sms) {
+                    pl.NC = nc;
+                    break;
+                }
             }
         }
-        if (best < 0) pl.NC = nc_max;
     }
     pl.n_nc = (m->n_p + pl.NC - 1) / pl.NC;
     pl.proj_ctas = m->num_sms;
