@@ -74,6 +74,10 @@ SPLIT_CASES = {
                                ("bf16x3", "bf16x6")),
     "two_phi_chunks_3x48x320_L6": (lambda: W.presn(n_r=3, n_theta=48, n_phi=320, L=6, r_lo=1e7, r_hi=1.5e7),
                                    ("bf16x3", "bf16x6")),
+    # 100 azimuthal cells in synthesis chunks of 64 columns: a ragged second chunk (its third
+    # 16-column store box holds 4 cells, its fourth none)
+    "ragged_phi_chunks_6x40x100_L6": (lambda: W.presn(n_r=6, n_theta=40, n_phi=100, L=6, r_lo=1e7, r_hi=2e7),
+                                      ("bf16x3", "bf16x6")),
     "monopole_L0_8x16x32": (lambda: W.presn(n_r=8, n_theta=16, n_phi=32, L=0), ("bf16x3",)),
     "random_rough_6x32x64_L8": (lambda: W.random_small((6, 32, 64), 8, seed=8, r0=0.2, r1=1.0), ("bf16x6",)),
     "many_moments_40x64x128_L50": (lambda: W.presn(n_r=40, n_theta=64, n_phi=128, L=50, r_lo=1e7, r_hi=3e7),
