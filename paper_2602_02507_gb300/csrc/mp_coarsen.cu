@@ -255,10 +255,9 @@ __global__ void __launch_bounds__(kCoarsenThreads, 6) k_coarsen(const CoarsenArg
     }
     // wider blocks (a power of two above 64, above 32 on unaligned fields, or the whole
     // ring): threads again take columns along phi (two at a time when aligned) and sum them
-    // over the polar block; each warp
-    // reduces its chunk of 32 V columns, and one thread per azimuthal block adds its chunks
-    // in order (a chunk never straddles two blocks: cp is a multiple of 32 V, or the block
-    // is the whole ring)
+    // over the polar block; each warp reduces its chunk of 32 V columns, and one thread per
+    // azimuthal block adds its chunks in order (a chunk never straddles two blocks: cp is a
+    // multiple of 32 V, or the block is the whole ring)
     double *chunk = reinterpret_cast<double *>(dsm);  // per chunk of 32 V columns: num, den; then per block: the mean
     constexpr int V = VEC;
     const int per_warp = 32 * V, warp = threadIdx.x >> 5;
