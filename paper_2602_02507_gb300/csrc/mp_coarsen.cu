@@ -145,6 +145,7 @@ __device__ __forceinline__ void coarsen_run(double *fld, const int4 *__restrict_
 // last chunk (a counter per entry and field, reset by that CTA) adds the chunks' sums in
 // chunk order, forms each azimuthal block's mean sum dphi_k S_k / sum dphi_k (any block
 // width) and writes it to every cell of the block.  No CTA waits for another.
+template <int V>
 __device__ __forceinline__ void coarsen_chunk(double *fld, const CoarsenArgs &a, int4 d, double *sm)
 {
     const int nthr = (int)blockDim.x, tid = (int)threadIdx.x, n_t = a.n_t, n_p = a.n_p;
@@ -154,17 +155,24 @@ __device__ __forceinline__ void coarsen_chunk(double *fld, const CoarsenArgs &a,
     double *base = fld + ((long long)wk.x * n_t + j0) * n_p;
     const double *w_th = a.nth + (size_t)((ct & (ct - 1)) == 0 ? __ffs(ct) - 1 : a.n_th_rows - 1) * n_t + j0;
     double *part = a.scratch + ((long long)blockIdx.y * a.n_scratch_rows + d.z) * n_p;
-    for (int k = 2 * tid; k < n_p; k += 2 * nthr) {
+    for (int k = V * tid; k < n_p; k += V * nthr) {
         double c0 = 0.0, c1 = 0.0;
 #pragma unroll
         for (int r = 0; r < kStageRows; ++r)
             if (r < nr) {
-                const double2 v = *reinterpret_cast<const double2 *>(base + (long long)(r0 + r) * n_p + k);
                 const double w = __ldg(w_th + r0 + r);
-                c0 = fma(w, v.x, c0);
-                c1 = fma(w, v.y, c1);
+                if (V == 2) {
+                    const double2 v = *reinterpret_cast<const double2 *>(base + (long long)(r0 + r) * n_p + k);
+                    c0 = fma(w, v.x, c0);
+                    c1 = fma(w, v.y, c1);
+                } else {
+                    c0 = fma(w, base[(long long)(r0 + r) * n_p + k], c0);
+                }
             }
-        __stcg(reinterpret_cast<double2 *>(part + (long long)d.y * n_p + k), make_double2(c0, c1));
+        if (V == 2)
+            __stcg(reinterpret_cast<double2 *>(part + (long long)d.y * n_p + k), make_double2(c0, c1));
+        else
+            __stcg(part + (long long)d.y * n_p + k, c0);
     }
     __threadfence();
     __syncthreads();
@@ -196,16 +204,27 @@ __device__ __forceinline__ void coarsen_chunk(double *fld, const CoarsenArgs &a,
         if (lane == 0) sM[b] = num / den;  // one division per block
     }
     __syncthreads();
-    for (int k = 2 * tid; k < n_p; k += 2 * nthr) {
-        const double2 out = make_double2(sM[k / cp], sM[(k + 1) / cp]);
-        for (int j = 0; j < ct; ++j) *reinterpret_cast<double2 *>(base + (long long)j * n_p + k) = out;
+    if (V == 2) {
+        for (int k = 2 * tid; k < n_p; k += 2 * nthr) {
+            const double2 out = make_double2(sM[k / cp], sM[(k + 1) / cp]);
+            for (int j = 0; j < ct; ++j) *reinterpret_cast<double2 *>(base + (long long)j * n_p + k) = out;
+        }
+    } else if (n_p >= nthr) {
+        for (int k = tid; k < n_p; k += nthr)  // one column a thread
+            for (int j = 0; j < ct; ++j) base[(long long)j * n_p + k] = sM[k / cp];
+    } else {
+        // fewer columns than threads (n_phi = 1 on 2-D meshes): the rows are dealt out too
+        const int per = nthr / n_p, k = tid % n_p, j1 = tid / n_p;
+        if (j1 < per)
+            for (int j = j1; j < ct; j += per) base[(long long)j * n_p + k] = sM[k / cp];
     }
     if (tid == 0) *cnt = 0;  // ready for the next launch
 }
 
-// VEC = 2 (16-byte aligned fields, even n_phi): the CTAs take, in this order, one chunk of a
-// block of many rows each, one entry of a wide block each (a power of two above 64 cells, or
-// the whole ring) and one run of groups[] each.  VEC = 1: one entry per CTA, all of them.
+// The CTAs take, in this order, one chunk of a block of many rows each, then, for VEC = 2
+// (16-byte aligned fields, even n_phi), one entry of a wide block each (a power of two above
+// 64 cells, or the whole ring) and one run of groups[] each; for VEC = 1, one entry of every
+// other block each.
 template <int VEC>
 __global__ void __launch_bounds__(kCoarsenThreads, 6) k_coarsen(const CoarsenArgs a)
 {
@@ -213,12 +232,12 @@ __global__ void __launch_bounds__(kCoarsenThreads, 6) k_coarsen(const CoarsenArg
     double *fld = a.f + (long long)blockIdx.y * a.stride;
     const int n_t = a.n_t, n_p = a.n_p;
     int x = (int)blockIdx.x;
+    if (x < a.n_chunk_ctas) {
+        coarsen_chunk<VEC>(fld, a, a.chunks[x], reinterpret_cast<double *>(dsm));
+        return;
+    }
+    x -= a.n_chunk_ctas;
     if (VEC == 2) {
-        if (x < a.n_chunk_ctas) {
-            coarsen_chunk(fld, a, a.chunks[x], reinterpret_cast<double *>(dsm));
-            return;
-        }
-        x -= a.n_chunk_ctas;
         if (x >= a.n_wide_ctas) {
             coarsen_run(fld, a.work, a.groups[x - a.n_wide_ctas], a.nph, a.nth, a.n_th_rows, n_t, n_p,
                         reinterpret_cast<double2 *>(dsm));
@@ -479,7 +498,8 @@ cudaError_t launch_coarsen(mp_mesh *m, double *fields, int n_fields, long long s
     const int per_warp = 32 * vec;
     const int n_chunks = (m->n_p + per_warp - 1) / per_warp;
     size_t smem = (size_t)3 * n_chunks * sizeof(double);
-    if (vec == 2) smem = std::max({smem, (size_t)kStageRows * threads * 16, (size_t)2 * m->n_p * sizeof(double)});
+    smem = std::max(smem, (size_t)2 * m->n_p * sizeof(double));
+    if (vec == 2) smem = std::max(smem, (size_t)kStageRows * threads * 16);
     if (smem > 48 * 1024) {
         const cudaError_t e = vec == 2 ? cudaFuncSetAttribute(k_coarsen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                                        : cudaFuncSetAttribute(k_coarsen<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -505,22 +525,20 @@ cudaError_t launch_coarsen(mp_mesh *m, double *fields, int n_fields, long long s
     a.n_p = m->n_p;
     a.n_big = m->n_cbig;
     a.n_scratch_rows = m->n_cscratch_rows;
-    if (vec == 2) {
-        // chunks of many-row blocks, then wide blocks one per CTA, then runs; kFieldBatch fields
-        // a launch (the scratch and counters are per field of a launch)
-        a.e_wide_first = m->n_cwork_fast;
-        a.n_chunk_ctas = m->n_cchunks;
-        a.n_wide_ctas = m->n_cwork_wide;
-        const unsigned gx = (unsigned)(m->n_cchunks + m->n_cwork_wide + m->n_cgroups);
-        for (int f0 = 0; f0 < n_fields; f0 += kFieldBatch) {
-            a.f = fields + (long long)f0 * stride;
-            k_coarsen<2><<<dim3(gx, (unsigned)std::min(kFieldBatch, n_fields - f0)), threads, smem, m->stream>>>(a);
-        }
-    } else {
-        a.e_wide_first = 0;
-        a.n_chunk_ctas = 0;
-        a.n_wide_ctas = m->n_cwork;
-        k_coarsen<1><<<dim3((unsigned)m->n_cwork, (unsigned)n_fields), threads, smem, m->stream>>>(a);
+    // chunks of many-row blocks first, then (aligned) wide blocks one per CTA and runs, or
+    // (unaligned) every other block one per CTA; kFieldBatch fields a launch (the scratch and
+    // counters are per field of a launch)
+    a.n_chunk_ctas = m->n_cchunks;
+    a.e_wide_first = vec == 2 ? m->n_cwork_fast : 0;
+    a.n_wide_ctas = vec == 2 ? m->n_cwork_wide : m->n_cwork_fast + m->n_cwork_wide;
+    const unsigned gx = (unsigned)(m->n_cchunks + a.n_wide_ctas + (vec == 2 ? m->n_cgroups : 0));
+    for (int f0 = 0; f0 < n_fields; f0 += kFieldBatch) {
+        a.f = fields + (long long)f0 * stride;
+        const dim3 grid(gx, (unsigned)std::min(kFieldBatch, n_fields - f0));
+        if (vec == 2)
+            k_coarsen<2><<<grid, threads, smem, m->stream>>>(a);
+        else
+            k_coarsen<1><<<grid, threads, smem, m->stream>>>(a);
     }
     prof_end(m, "coarsen_blocks", ev);
     return cudaGetLastError();
