@@ -28,7 +28,8 @@
 //   * the rest (power-of-two azimuthal blocks up to 64 cells): runs of consecutive
 //     entries of at most kStageRows rows, all their rows copied to shared memory by
 //     cp.async at once, two columns a thread, shuffles within each azimuthal block.
-// Otherwise one CTA per entry, one column a thread.  Every coarsened cell is read
+// On other fields (odd n_phi, 2-D meshes, odd offsets) the same chunks for blocks of
+// many rows, then one CTA per entry, one column a thread.  Every coarsened cell is read
 // once and written once.  Float64 throughout.
 #include <algorithm>
 #include <cmath>
