@@ -14,7 +14,8 @@
 // cell itself and its one neighbour.  A single cell along a coordinate, or two
 // azimuthal cells on a full circle, give a zero derivative.
 //
-// One block per (shell, polar cell) row; threads along phi.  The potential is
+// One block per (shell, polar cell) row, threads along phi (rows of fewer than 32 cells:
+// one thread per cell over the flattened mesh).  The potential is
 // read through the cache (each value serves the six neighbouring differences:
 // rows j +- 1 and shells i +- 1 are read by nearby blocks while they are still
 // in L2); density, velocity and the outputs stream once (evict-first).  All
@@ -64,6 +65,41 @@ __global__ void __launch_bounds__(256) k_gravity(const double *__restrict__ phi,
             const double vg = fma(__ldcs(v + 2 * N + c), g2, fma(__ldcs(v + N + c), g1, __ldcs(v + c) * g0));
             __stcs(E + c, nr * vg);
         }
+    }
+}
+
+// The same sources with one thread per cell over the flattened mesh, for rows shorter than
+// a warp (2-D meshes have one azimuthal cell: a block per row would hold one busy thread).
+__global__ void __launch_bounds__(256) k_gravity_flat(const double *__restrict__ phi, const double *__restrict__ rho,
+                                                      const double *__restrict__ v, double *__restrict__ grad,
+                                                      double *__restrict__ S, double *__restrict__ E,
+                                                      const GradStencil *__restrict__ st, int n_r, int n_t,
+                                                      int n_p, long long N)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const long long row = c / n_p;
+    const int k = (int)(c - row * n_p);
+    const int i = (int)(row / n_t), j = (int)(row - (long long)i * n_t);
+    const GradStencil gr = st[i], gt = st[n_r + j], gp = st[n_r + n_t + k];
+    const double *p_r = phi + (long long)j * n_p + k, *p_t = phi + (long long)i * n_t * n_p + k;
+    const double g0 = (__ldg(p_r + (long long)gr.hi * n_t * n_p) - __ldg(p_r + (long long)gr.lo * n_t * n_p)) * gr.w;
+    const double g1 = (__ldg(p_t + (long long)gt.hi * n_p) - __ldg(p_t + (long long)gt.lo * n_p)) * gt.w;
+    const double g2 = (__ldg(phi + row * n_p + gp.hi) - __ldg(phi + row * n_p + gp.lo)) * gp.w;
+    if (grad) {
+        grad[c] = g0;
+        grad[N + c] = g1;
+        grad[2 * N + c] = g2;
+    }
+    const double nr = -rho[c];
+    if (S) {
+        const double s0 = nr * g0, s1 = nr * g1, s2 = nr * g2;
+        S[c] = s0;
+        S[N + c] = s1;
+        S[2 * N + c] = s2;
+        if (E) E[c] = fma(v[2 * N + c], s2, fma(v[N + c], s1, v[c] * s0));
+    } else if (E) {
+        E[c] = nr * fma(v[2 * N + c], g2, fma(v[N + c], g1, v[c] * g0));
     }
 }
 
@@ -119,9 +155,14 @@ cudaError_t launch_gravity(mp_mesh *m, const double *phi, const double *rho, con
 {
     cudaEvent_t ev;
     prof_begin(m, "gravity_sources", &ev);
-    const int threads = std::min(256, 32 * ((m->n_p + 31) / 32));
-    k_gravity<<<(unsigned)m->R, threads, 0, m->stream>>>(phi, rho, v, grad, S, E, m->d_gst, m->n_r, m->n_t, m->n_p,
-                                                         m->N);
+    if (m->n_p < 32) {
+        k_gravity_flat<<<(unsigned)((m->N + 255) / 256), 256, 0, m->stream>>>(phi, rho, v, grad, S, E, m->d_gst, m->n_r,
+                                                                              m->n_t, m->n_p, m->N);
+    } else {
+        const int threads = std::min(256, 32 * ((m->n_p + 31) / 32));
+        k_gravity<<<(unsigned)m->R, threads, 0, m->stream>>>(phi, rho, v, grad, S, E, m->d_gst, m->n_r, m->n_t,
+                                                             m->n_p, m->N);
+    }
     prof_end(m, "gravity_sources", ev);
     return cudaGetLastError();
 }
