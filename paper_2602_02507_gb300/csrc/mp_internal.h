@@ -30,7 +30,7 @@ struct SplitPlan {
     int n_kc = 0;         // projection K chunks of 16 azimuthal cells
     int Kpad = 0;         // synthesis GEMM K: 2L rounded up to 16 (m >= 1 columns)
     int ldF = 0;          // theta contraction: padded polar-cell row of F and Ith32
-    int NC = 0;           // synthesis GEMM N per chunk: min(256, n_phi rounded to 16)
+    int NC = 0;           // synthesis GEMM N per work unit: 64, 128 or 256 (n_phi rounded to 16 below 64)
     int n_nc = 0;         // synthesis N chunks
     int proj_ctas = 0;    // persistent grid sizes
     int synth_ctas = 0;
