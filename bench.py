@@ -54,7 +54,7 @@ SPLIT_PRECISION = "bf16x3"
 #               source file of the kernel, sha1 of that file and the shared headers at
 #               capture time); an entry whose sources changed since is ignored
 NCU_TRAFFIC = {
-    "split_phi_project_tc": (134322944 + 3294976, "mp_split.cu", "0daff66ddc57a6367dfeaddb11960824e8dfdc09"),
+    "split_phi_project_tc": (134318592 + 3101952, "mp_split.cu", "055b2c945b2aba8b5d946b7478e317e01773fdc1"),
 }
 KERNEL_HEADERS = ("ptx.cuh", "mp_internal.h", "mp_errors.h")
 
