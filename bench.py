@@ -1,26 +1,33 @@
 #!/usr/bin/env python
 """Benchmark of the multipole Poisson solve on one GB300 (or N replicas).
 
-Workload: presupernova-like core, 512 x 128 x 256 cells (geometric shells over
-[1e5, 1e10] cm), l_max = 16, density rho_c/(1+(r/r_c)^2)^1.5 times seeded
-l <= 4 harmonic perturbations (seed 2).  One step = one full solve (moments,
-radial recurrences, potential) of that density, resident in HBM, through the
-C ABI (mp_solve) on the split-precision BF16x3 tensor-core path.
+Headline workload (default): the large single solve, 2048 x 512 x 1024 cells (1.07e9),
+geometric shells over [1e5, 1e10] cm, l_max = 64, density rho_c/(1+(r/r_c)^2)^1.5 times
+seeded harmonic perturbations (l <= 4 at 1e-2, l <= 64 at 1e-3; seed 4).  One step = one
+full solve (moments, radial recurrences, potential) of that density, resident in HBM,
+through the C ABI (mp_solve) on the split-precision BF16x3 tensor-core path.
 
-Also reported on the same line: the float64 GPU path on the same workload,
-the accuracy of both against the FP64 CPU oracle, an end-to-end number with
-pinned host buffers (mp_solve_host_async: every step copies rho host->device,
-solves and copies Phi device->host; one step's download overlaps the next step's
-upload), per-kernel timing with the dominant kernel's HBM roofline fraction,
-SM clocks sampled during the timed region, and the oracle timed on the host
-cores as a CPU baseline.
+The timed region repeats blocks of K solves (each block bracketed by a barrier and a
+device synchronize) until about a second of device time has passed, so that the clock
+sampler sees the load; ms_per_step is the median block time / K.  Also on the line: the
+float64 GPU path on the same density, the accuracy of both against the FP64 CPU oracle
+(Phi pointwise over every cell, the angular and edge moments per degree), per-kernel
+times with the dominant kernel's HBM roofline and the tensor-pipe fraction of the two
+tcgen05 contractions, an end-to-end number (mp_solve_host_async with pinned host
+buffers: every step copies rho host->device and Phi device->host), SM clocks sampled
+during the timed region, the oracle on the host cores (all threads: one whole solve;
+one thread: a slab of shells) as the CPU baseline, and the other workloads (presupernova
+512x128x256 L=16, log-normal 1024x256x512 L=32, homogeneous spheroid 64x32x64 L=8, and
+the batch of 64 uneven meshes) with their own accuracy and HBM fractions.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload large|presn|lognormal|spheroid] [--lean]
 
-With N > 1 the script runs under torch.distributed.run, one rank per GPU, each
-rank solving its own replica of the workload (no data exchange); the job value
-is the total solves/s over ranks timed by the slowest rank.  --impl reference
-times the FP64 CPU oracle on the host cores instead (rank 0 only).
+With N > 1 the script runs under torch.distributed.run, one rank per GPU, each rank
+solving its own replica of the workload (no data exchange); the job value is the total
+solves/s over ranks timed by the slowest rank.  --impl reference times the FP64 CPU
+oracle on the host cores instead (rank 0 only).  --lean times the split path alone
+(no oracle, float64 path, end-to-end leg or side workloads), for profiler runs.
 """
 from __future__ import annotations
 
@@ -41,21 +48,21 @@ if ROOT not in sys.path:
 
 METRIC = "Poisson solves/s & Gcell*mode/s, BF16x3 vs FP64 GPU at <=1e-6 rel err in Phi"
 WORKLOADS = {
-    # the benchmarked configuration (default)
+    # the headline configuration (default): the largest single-GPU configuration
+    "large": "large single solve 2048x512x1024 cells (1.07e9), geometric r in [1e5,1e10] cm, l_max=64, "
+             "presn profile x (1 + l<=4 harmonics at 1e-2 + l<=64 harmonics at 1e-3), seed 4",
     "presn": "presupernova core 512x128x256 cells, geometric r in [1e5,1e10] cm, l_max=16, seed 2",
-    # a larger one for measurement and profiling of the large-table kernels
     "lognormal": "log-normal angular field 1024x256x512 cells, geometric r in [1e5,1e12] cm, l_max=32, seed 3",
+    "spheroid": "homogeneous oblate spheroid a1=1, a3=0.6, 64x32x64 uniform cells over r in [0,1.5], l_max=8, G=1",
 }
+BATCH_DESC = ("64 uneven meshes (n_r,n_theta,n_phi) from {(256,64,128),(512,128,256),(768,192,384),"
+              "(1024,256,512)}, l_max from {8,16,32}, presn densities with per-mesh rho_c, r_c, seed 5")
 SPLIT_PRECISION = "bf16x3"
 
-# DRAM bytes (read + write) per launch from one ncu capture of the same
-# workload, valid while the kernel source hashes match.
-# kernel name: (DRAM bytes read + written per launch from one ncu capture (profiles/),
-#               source file of the kernel, sha1 of that file and the shared headers at
-#               capture time); an entry whose sources changed since is ignored
-NCU_TRAFFIC = {
-    "split_phi_project_tc": (134318592 + 3101952, "mp_split.cu", "055b2c945b2aba8b5d946b7478e317e01773fdc1"),
-}
+# (workload, kernel): (DRAM bytes read + written per launch from one ncu capture (profiles/),
+#                      source file of the kernel, sha1 of that file and the shared headers at
+#                      capture time); an entry whose sources changed since is ignored
+NCU_TRAFFIC = {}
 KERNEL_HEADERS = ("ptx.cuh", "mp_internal.h", "mp_errors.h")
 
 
@@ -66,12 +73,13 @@ def log(*a):
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10000)
-    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU-baseline budget")
-    p.add_argument("--workload", choices=sorted(WORKLOADS), default="presn",
-                   help="mesh and density (presn is the benchmarked configuration)")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="large",
+                   help="mesh and density of the headline (large is the benchmarked configuration)")
+    p.add_argument("--min-seconds", type=float, default=1.0, help="device time the timed blocks fill")
+    p.add_argument("--lean", action="store_true", help="split path timing only (profiler runs)")
     return p.parse_args()
 
 
@@ -83,13 +91,15 @@ def dist_info():
 
 
 def measured_peaks():
+    """(HBM GB/s, bf16 TFLOP/s sustained, kind): the measured peaks of this machine's
+    GB300s, else the fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 1700.0, "fallback"
 
 
 def source_hash(source: str):
@@ -132,7 +142,9 @@ class ClockSampler:
             log("clock sampler unavailable:", e)
             self.proc = None
 
-    def stop(self):
+    def stop(self, skip_s: float = 0.0):
+        """Clock summary of the samples taken after the first skip_s seconds (the idle lead-in
+        before the timed region)."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         self.proc.terminate()
@@ -158,60 +170,229 @@ class ClockSampler:
                     if v.lower().startswith("active"):
                         reasons.add(n)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm),
+        skip = min(len(sm) - 1, int(skip_s / 0.1)) if sm else 0
+        load = sm[skip:]
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_under_load": len(load),
                 "power_w_max": max(power) if power else None}
 
 
-# ---------------------------------------------------------------- oracle timing
-def cpu_baseline_leg(w, budget_s: float, max_reps: int = 200):
-    """The oracle on the host cores: solves of the workload for about budget_s seconds.
-    Returns (solves/s, solves, seconds, threads, Phi of the first solve); that Phi is the
-    reference the GPU paths' accuracy is stated against."""
+# ---------------------------------------------------------------- workloads
+def make_workload(name):
+    """Mesh and host density of a headline workload (seeded, synthetic)."""
+    from paper_2602_02507_gb300 import workloads as W
+    if name == "large":
+        return W.large(materialize=True)
+    return getattr(W, name)()
+
+
+# ---------------------------------------------------------------- oracle leg (host cores)
+def oracle_reference(w, want_phi=True):
+    """One FP64 oracle solve of the whole workload on every host thread: (result with the
+    oracle's tables, seconds, threads).  Its Phi and moments are the reference the GPU
+    paths' accuracy is stated against."""
     from oracle import oracle as O
     m = w.mesh
     tab = O.build_tables(m.r, m.theta, m.phi, m.L)
-    phi_ref = O.solve(tab, w.rho, m.G)["phi"]  # also warms caches and threads
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        O.solve(tab, w.rho, m.G)
-        reps += 1
+    t0 = time.perf_counter()
+    ref = O.solve(tab, w.rho, m.G, want_phi=want_phi)
+    el = time.perf_counter() - t0
+    ref["tables"] = tab
+    return ref, el, O.get_threads()
+
+
+def oracle_one_thread(w, tab, seconds_all, threads, target_s=3.0):
+    """The oracle on one host thread, timed on a slab of the workload's first shells (about
+    target_s seconds of work) and scaled to the whole mesh by its share of the shells:
+    (solves/s, shells, seconds)."""
+    from oracle import oracle as O
+    m = w.mesh
+    n_r = m.shape[0]
+    per_shell = seconds_all * threads / n_r
+    ns = int(max(1, min(n_r, round(target_s / max(per_shell, 1e-9)))))
+    WR, WI, V = O.radial_integrals(m.L, m.r[:ns + 1], tab.r_ref)
+    slab = O.Tables(r=m.r[:ns + 1], theta=tab.theta, phi=tab.phi, L=m.L, r_ref=tab.r_ref, Ith=tab.Ith,
+                    Iph=tab.Iph, WR=WR, WI=WI, V=V)
+    prev = O.get_threads()
+    O.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        O.solve(slab, w.rho[:ns], m.G)
         el = time.perf_counter() - t0
-        if el >= budget_s or reps >= max_reps:
-            break
-    return reps / el, reps, el, O.get_threads(), phi_ref
+    finally:
+        O.set_threads(prev)
+    return (ns / n_r) / el, ns, el
+
+
+def r3(xs):
+    return [float(f"{x:.3g}") for x in xs]
+
+
+def phi_error_vs_oracle(phi_dev, ref_phi, chunk=64):
+    """max over every cell of |Phi_gpu - Phi_oracle| / |Phi_oracle| (shells in chunks)."""
+    import numpy as np
+    n_r = ref_phi.shape[0]
+    g3 = phi_dev.view(n_r, -1)
+    err = 0.0
+    for i0 in range(0, n_r, chunk):
+        g = g3[i0:i0 + chunk].cpu().numpy().reshape(ref_phi[i0:i0 + chunk].shape)
+        r = ref_phi[i0:i0 + chunk]
+        err = max(err, float(np.max(np.abs(g - r) / np.abs(r))))
+    return err
+
+
+def phi_diff_on_device(a, b, chunk_cells=1 << 26):
+    """max |a - b| / |b| over two device potentials (chunked)."""
+    out = 0.0
+    fa, fb = a.view(-1), b.view(-1)
+    for c0 in range(0, fa.numel(), chunk_cells):
+        x, y = fa[c0:c0 + chunk_cells], fb[c0:c0 + chunk_cells]
+        out = max(out, float(((x - y).abs() / y.abs()).max().item()))
+    return out
+
+
+def moment_report(mesh, w, ref, S, prec):
+    """Per-degree errors of the exported moments against the oracle: angular moments and
+    edge moments relative to the sum of the magnitudes of each moment's terms (with the
+    split path's error-model bar), and angular moments relative to their degree's largest."""
+    import torch
+    from oracle.error_metrics import edge_term_errors, moment_term_errors, per_l_errors, split_moment_bar
+    m = w.mesh
+    n_r, K = m.shape[0], m.KL
+    A = torch.empty(n_r * K, dtype=torch.float64, device="cuda")
+    MR = torch.empty((n_r + 1) * K, dtype=torch.float64, device="cuda")
+    MI = torch.empty((n_r + 1) * K, dtype=torch.float64, device="cuda")
+    mesh.get_moments(A, MR, MI)
+    mesh.synchronize()
+    got = {"A": A.cpu().numpy().reshape(n_r, K), "MR": MR.cpu().numpy().reshape(n_r + 1, K),
+           "MI": MI.cpu().numpy().reshape(n_r + 1, K)}
+    eA = moment_term_errors(got["A"], ref["A"], S, m.L)
+    eM = edge_term_errors(got, ref, S)
+    eD = per_l_errors(got["A"], ref["A"], m.L)
+    bar = split_moment_bar(m, prec) if prec != "fp64" else 1e-12
+    return {"moments_bar_rel_terms": bar,
+            "max_over_l": {"A_rel_terms": max(eA), "MR_rel_terms": max(eM["MR"]), "MI_rel_terms": max(eM["MI"]),
+                           "A_rel_degree_max": max(eD)},
+            "within_bar": bool(max(eA + eM["MR"] + eM["MI"]) <= bar),
+            "per_l": {"A_rel_terms": r3(eA), "MR_rel_terms": r3(eM["MR"]), "MI_rel_terms": r3(eM["MI"]),
+                      "A_rel_degree_max": r3(eD)}}
+
+
+# ---------------------------------------------------------------- device timing
+def timed_blocks(solve, steps, min_seconds, stream, barrier, max_over_ranks):
+    """Device times (ms) of blocks of `steps` calls of solve(), each block bracketed by a
+    barrier and a device synchronize and timed with CUDA events on the launching stream;
+    blocks repeat until about min_seconds of device time (at least 3 blocks)."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def block():
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1)
+
+    times = [block()]
+    more = int(max_over_ranks(float(min(2000, max(2, math.ceil(min_seconds * 1e3 / max(times[0], 1e-3)) - 1)))))
+    times += [block() for _ in range(more)]
+    return times
+
+
+# ---------------------------------------------------------------- roofline bookkeeping
+def alg_bytes(kernel: str, cells: int, rows: int, n_r: int, L: int, KL: int):
+    """Algorithmic DRAM bytes per launch: the step's inputs read once and outputs written
+    once.  The two streaming steps count the density read (8 B/cell) and the potential
+    write (8 B/cell); the intermediates of the other kernels are listed for reference."""
+    P = 2 * L + 1
+    table = {
+        "split_phi_project_tc": 8 * cells,                       # rho in (step (a) reads S once)
+        "split_synth_tc": 8 * cells,                             # Phi out (step (d) writes Phi once)
+        "split_theta_contract": 4 * rows * P + 8 * n_r * KL,     # F in, moments out
+        "radial_scan": 8 * n_r * KL * 2 + 16 * (n_r + 1) * KL + 4 * n_r * KL,
+        "split_theta_synth": rows * (4 * ((2 * L + 15) // 16 * 16) + 8),
+        "fp64_phi_project": 8 * cells + 8 * rows * P,
+        "fp64_theta_contract": 8 * rows * P + 8 * n_r * KL,
+        "fp64_theta_synth": 8 * rows * P,
+        "fp64_phi_synth": 8 * cells + 8 * rows * P,
+    }
+    return table.get(kernel)
+
+
+def mma_flops(kernel: str, shape, L: int, nprod: int):
+    """(useful, executed) tensor-core flops per launch of the two tcgen05 contractions:
+    useful = bf16 products x 2 x cells x columns; executed uses the padded GEMM dimensions
+    (projection N = 2L+1 rounded up to 16, K = n_phi rounded up to 32; synthesis K = 2L
+    rounded up to 16, N = n_phi rounded up to 16)."""
+    n_r, n_t, n_p = shape
+    rows = n_r * n_t
+    rows_pad = -(-rows // 128) * 128
+    if kernel == "split_phi_project_tc":
+        useful = nprod * 2 * rows * n_p * (2 * L + 1)
+        executed = nprod * 2 * rows_pad * (-(-n_p // 32) * 32) * (-(-(2 * L + 1) // 16) * 16)
+    elif kernel == "split_synth_tc":
+        useful = nprod * 2 * rows * n_p * (2 * L)
+        executed = nprod * 2 * rows_pad * (-(-n_p // 16) * 16) * max(16, -(-(2 * L) // 16) * 16)
+    else:
+        return None
+    return useful, executed
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The FP64 CPU oracle on the host cores, on the headline workload: each step solves a
+    bounded sample of it (the whole mesh when one solve takes under half a second, else a
+    slab of its first shells sized to about half a second), scaled to whole solves by the
+    sample's share of the shells."""
     world, rank, _ = dist_info()
     if rank != 0:
         return 0
+    import numpy as np
     from oracle import build as oracle_build
     from oracle import oracle as O
-    from paper_2602_02507_gb300 import workloads as W
     oracle_build.build()
-    w = getattr(W, args.workload)()
+    w = make_workload(args.workload)
     m = w.mesh
+    n_r = m.shape[0]
     tab = O.build_tables(m.r, m.theta, m.phi, m.L)
-    for _ in range(args.warmup):
-        O.solve(tab, w.rho, m.G)
-    steps = max(1, min(args.steps, 30))
+    # size the sample: time one shell-slab solve, grow it to about half a second
+    ns = max(1, n_r // 256)
+    while True:
+        WR, WI, V = O.radial_integrals(m.L, m.r[:ns + 1], tab.r_ref)
+        slab = O.Tables(r=m.r[:ns + 1], theta=tab.theta, phi=tab.phi, L=m.L, r_ref=tab.r_ref, Ith=tab.Ith,
+                        Iph=tab.Iph, WR=WR, WI=WI, V=V)
+        rho = np.ascontiguousarray(w.rho[:ns])
+        t0 = time.perf_counter()
+        O.solve(slab, rho, m.G)
+        el = time.perf_counter() - t0
+        if el >= 0.25 or ns == n_r:
+            break
+        ns = min(n_r, max(ns + 1, int(ns * 0.5 / max(el, 1e-3))))
+    warm = min(args.warmup, 2)
+    for _ in range(warm):
+        O.solve(slab, rho, m.G)
+    steps = max(1, args.steps)
     t0 = time.perf_counter()
     for _ in range(steps):
-        O.solve(tab, w.rho, m.G)
+        O.solve(slab, rho, m.G)
     el = time.perf_counter() - t0
-    value = steps / el
-    sample = f"the whole workload per step: factored FP64 oracle solve, tables prebuilt, {steps} steps"
+    value = steps * (ns / n_r) / el
+    sample = (f"FP64 oracle (tables prebuilt), each step the first {ns} of {n_r} shells "
+              f"({ns / n_r:.4g} of the workload), {steps} steps in {el:.2f} s, scaled by shells")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "precision": "fp64 (CPU oracle)", "cells": m.cells,
                    "l_max": m.L},
         "gcell_mode_per_s": value * m.cells * m.KL / 1e9,
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": O.get_threads(), "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -236,24 +417,199 @@ def whole_job_rate(world: int, steps: int, total_ms: float) -> float:
     return world * steps / (total_ms * 1e-3)
 
 
+# ---------------------------------------------------------------- side workloads
+def side_workload(name, args, stream, with_oracle, hbm_peak):
+    """One of the other configurations: split and float64 GPU solves timed (blocks filling
+    about 0.3 s), their accuracy against the oracle, the whole-step HBM fraction."""
+    import numpy as np
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = make_workload(name)
+    m = w.mesh
+    rho = torch.from_numpy(np.ascontiguousarray(w.rho)).cuda()
+    out = {"workload": WORKLOADS[name], "cells": m.cells, "l_max": m.L}
+    nothing = lambda: None  # noqa: E731
+    ident = lambda x: x  # noqa: E731
+    for prec in (SPLIT_PRECISION, "fp64"):
+        phi = torch.empty_like(rho)
+        with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=prec, stream=stream) as mesh:
+            mesh.set_density(rho)
+            mesh.set_phi_output(phi)
+            for _ in range(3):
+                mesh.solve()
+            mesh.synchronize()
+            steps = max(args.steps, 20) if prec != "fp64" else 5
+            times = timed_blocks(mesh.solve, steps, 0.3 if prec != "fp64" else 0.2, stream, nothing, ident)
+            mesh.synchronize()
+            ms = statistics.median(times) / steps
+            key = "split" if prec != "fp64" else "fp64_gpu"
+            out[key] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms,
+                        "hbm_frac_16B_per_cell": 16 * m.cells / (ms * 1e-3) / 1e9 / hbm_peak,
+                        "effective_precision": mesh.info()["effective_precision"]}
+            if with_oracle:
+                if "ref" not in out:
+                    ref, el, thr = oracle_reference(w)
+                    from oracle.error_metrics import term_scales
+                    out["_ref"], out["_S"] = ref, term_scales(w.rho, ref["tables"], m.G)
+                    out["oracle_solves_per_s"] = {"value": 1.0 / el, "threads": thr}
+                    out["ref"] = True
+                out[key]["phi_max_rel_err_vs_oracle"] = phi_error_vs_oracle(phi, out["_ref"]["phi"])
+                rep = moment_report(mesh, w, out["_ref"], out["_S"], prec)
+                rep.pop("per_l")
+                out[key].update(rep)
+        del phi
+    out.pop("ref", None)
+    out.pop("_ref", None)
+    out.pop("_S", None)
+    out["speedup_split_vs_fp64_gpu"] = out["fp64_gpu"]["ms_per_solve"] / out["split"]["ms_per_solve"]
+    del rho, w
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_workload(args, stream, with_oracle, hbm_peak):
+    """The 64 uneven meshes: one graph-launched batch (split path) against a loop of
+    per-mesh float64 solves; densities built on the device from their separable factors;
+    the smallest mesh of each l_max and the three smallest overall against the oracle."""
+    import numpy as np
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    from paper_2602_02507_gb300 import workloads as W
+    draws = W.batch_draws()
+    meshes, meshes64, rhos, phis, phis64, cells = [], [], [], [], [], 0
+    for n in range(len(draws)):
+        w = W.batch_instance(n, draws, materialize=False)
+        m = w.mesh
+        prof = torch.from_numpy(w.extra["profile"]).cuda()
+        ang = torch.from_numpy(w.extra["angular"]).cuda()
+        rho = (prof[:, None, None] * ang[None, :, :]).contiguous()
+        phi, phi64 = torch.empty_like(rho), torch.empty_like(rho)
+        ms = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=SPLIT_PRECISION, stream=stream)
+        ms.set_density(rho)
+        ms.set_phi_output(phi)
+        m64 = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="fp64", stream=stream)
+        m64.set_density(rho)
+        m64.set_phi_output(phi64)
+        meshes.append(ms)
+        meshes64.append(m64)
+        rhos.append(rho)
+        phis.append(phi)
+        phis64.append(phi64)
+        cells += m.cells
+    batch = mpl.Batch(meshes)
+    for _ in range(3):
+        batch.solve()
+    torch.cuda.synchronize()
+    nothing = lambda: None  # noqa: E731
+    ident = lambda x: x  # noqa: E731
+    times = timed_blocks(batch.solve, max(5, args.steps // 4), 0.5, stream, nothing, ident)
+    ms = statistics.median(times) / max(5, args.steps // 4)
+
+    def loop64():
+        for mm in meshes64:
+            mm.solve()
+
+    loop64()
+    torch.cuda.synchronize()
+    t64 = statistics.median(timed_blocks(loop64, 1, 0.2, stream, nothing, ident))
+    out = {"workload": BATCH_DESC, "instances": len(draws), "cells": cells,
+           "split": {"batches_per_s": 1e3 / ms, "ms_per_batch": ms,
+                     "hbm_frac_16B_per_cell": 16 * cells / (ms * 1e-3) / 1e9 / hbm_peak,
+                     "launch": "one CUDA graph launch per batch"},
+           "fp64_gpu": {"ms_per_batch": t64, "launch": "per-mesh float64 solves in a loop"},
+           "speedup_split_vs_fp64_gpu": t64 / ms}
+    if with_oracle:
+        order = sorted(range(len(draws)), key=lambda n: np.prod(draws[n][0]) * draws[n][1])
+        picks = list(order[:3])
+        for L in sorted({d[1] for d in draws}):
+            n = min((k for k in range(len(draws)) if draws[k][1] == L), key=lambda k: np.prod(draws[k][0]))
+            if n not in picks:
+                picks.append(n)
+        worst = 0.0
+        for n in picks:
+            w = W.batch_instance(n, draws)
+            ref, _, _ = oracle_reference(w)
+            worst = max(worst, phi_error_vs_oracle(phis[n], ref["phi"]))
+        out["split"]["phi_max_rel_err_vs_oracle"] = worst
+        out["split"]["oracle_checked_instances"] = [f"{draws[n][0]} L={draws[n][1]}" for n in picks]
+    out["split"]["phi_max_rel_err_vs_fp64_gpu"] = max(phi_diff_on_device(a, b) for a, b in zip(phis, phis64))
+    batch.close()
+    for mm in meshes + meshes64:
+        mm.close()
+    del rhos, phis, phis64
+    torch.cuda.empty_cache()
+    return out
+
+
+def beside_solve(stream, hbm_peak, rates, steps):
+    """Gravitational source terms (Sec. 3) of a presupernova solve's potential and the
+    coarsening-block averaging on the paper's N_theta = 256 mesh: float64 kernels bound by
+    the float64 pipe, timed beside (not inside) the solve."""
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    from paper_2602_02507_gb300 import workloads as W
+    w = W.presn()
+    m = w.mesh
+    cells = m.cells
+    rho = torch.from_numpy(w.rho).cuda()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    mesh = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=SPLIT_PRECISION, stream=stream)
+    mesh.set_density(rho)
+    mesh.solve()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    gvel = torch.randn(3 * cells, dtype=torch.float64, device="cuda", generator=gen)
+    gS = torch.empty(3 * cells, dtype=torch.float64, device="cuda")
+    gE = torch.empty(cells, dtype=torch.float64, device="cuda")
+    kg = max(10, steps)
+    for _ in range(2):
+        mesh.gravity_sources(v=gvel, S=gS, E=gE)
+    mesh.synchronize()
+    e0.record(stream)
+    for _ in range(kg):
+        mesh.gravity_sources(v=gvel, S=gS, E=gE)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_us = e0.elapsed_time(e1) / kg * 1e3
+    fp64_instr_peak = rates["fp64_tflops"] * 1e12 / 2.0  # one FMA instruction = 2 flops
+    gravity = {"kernel": "gravity_sources", "workload": WORKLOADS["presn"], "launches": kg, "avg_launch_us": g_us,
+               "algorithmic_bytes_per_cell": 72, "hbm_gbs": 72 * cells / g_us / 1e3,
+               "hbm_frac": 72 * cells / g_us / 1e3 / hbm_peak,
+               "fp64_instr_per_cell": 12, "fp64_instr_per_s": 12 * cells / (g_us * 1e-6),
+               "fp64_frac": 12 * cells / (g_us * 1e-6) / fp64_instr_peak, "bound": "fp64",
+               "note": "S [3] and E from Phi, rho, v [3]: 9 float64 reads + 4 writes per cell"}
+    mesh.close()
+    del gvel, gS, gE, rho
+    pm = W.paper_mesh(256, 0.25, 3.68, 0, 3)
+    cmesh = mpl.Mesh(pm.r, pm.theta, pm.phi, 2, 1.0, precision="fp64", stream=stream)
+    c_t, c_p = cmesh.coarsening_factors()
+    n_pm = (pm.r.size - 1) * (pm.theta.size - 1) * (pm.phi.size - 1)
+    coarse_cells = int(((c_t[:, None] > 1) | (c_p > 1)).sum()) * (pm.phi.size - 1)
+    cfield = torch.randn(n_pm, dtype=torch.float64, device="cuda", generator=gen)
+    kc = max(10, steps)
+    for _ in range(2):
+        cmesh.coarsen(cfield)
+    cmesh.synchronize()
+    e0.record(stream)
+    for _ in range(kc):
+        cmesh.coarsen(cfield)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    c_us = e0.elapsed_time(e1) / kc * 1e3
+    coarsen = {"kernel": "coarsen_blocks", "mesh": "paper rule N_theta = 256: 942 x 256 x 512",
+               "cells": n_pm, "coarsened_cells": coarse_cells, "launches": kc, "avg_launch_us": c_us,
+               "algorithmic_bytes": 16 * coarse_cells, "hbm_gbs": 16 * coarse_cells / c_us / 1e3,
+               "hbm_frac": 16 * coarse_cells / c_us / 1e3 / hbm_peak, "bound": "fp64",
+               "note": "every coarsened cell read once and written once (in place); the float64 pipe "
+                       "(about 1.6 float64 instructions a coarsened cell) bounds it before HBM"}
+    cmesh.close()
+    del cfield
+    torch.cuda.empty_cache()
+    return gravity, coarsen
+
+
 # ---------------------------------------------------------------- our arm
-def alg_bytes(kernel: str, cells: int, rows: int, n_r: int, L: int, KL: int):
-    """Algorithmic DRAM bytes per launch (each input read once, each output written once)."""
-    P = 2 * L + 1
-    table = {
-        "split_phi_project_tc": 8 * cells + 4 * rows * P,        # rho in, F out (float32, 2L+1 columns)
-        "split_synth_tc": 8 * cells,                             # Phi out (coefficients are L2-resident)
-        "split_theta_contract": 4 * rows * P + 8 * n_r * KL,     # F in, moments out
-        "radial_scan": 8 * n_r * KL * 2 + 16 * (n_r + 1) * KL + 4 * n_r * KL,  # A in; C, MR, MI, C32 out
-        "split_theta_synth": rows * (4 * ((2 * L + 15) // 16 * 16) + 4),       # bf16 x2 G terms + m = 0 column out
-        "fp64_phi_project": 8 * cells + 8 * rows * P,
-        "fp64_theta_contract": 8 * rows * P + 8 * n_r * KL,
-        "fp64_theta_synth": 8 * rows * P,
-        "fp64_phi_synth": 8 * cells + 8 * rows * P,
-    }
-    return table.get(kernel)
-
-
 def run_ours(args):
     import numpy as np
     import torch
@@ -267,7 +623,6 @@ def run_ours(args):
     import __graft_entry__ as g
     g.build()
     from paper_2602_02507_gb300 import multipole as mpl
-    from paper_2602_02507_gb300 import workloads as W
 
     def barrier():
         if world > 1:
@@ -276,36 +631,54 @@ def run_ours(args):
     def max_over_ranks(x: float) -> float:
         return max_over_ranks_on(x, world, "cuda")
 
-    w = getattr(W, args.workload)()
+    hbm_peak, tc_peak, peak_kind = measured_peaks()
+    full = not args.lean
+    with_oracle = full and rank == 0 and world == 1
+    w = make_workload(args.workload)
     m = w.mesh
     cells, KL = m.cells, m.KL
     rows = m.shape[0] * m.shape[1]
     stream = torch.cuda.current_stream()
     rho = torch.from_numpy(w.rho).cuda()
     phi = torch.empty_like(rho)
-    phi64 = torch.empty_like(rho)
     mesh = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=SPLIT_PRECISION, stream=stream)
-    mesh64 = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="fp64", stream=stream)
-    for ms_, out in ((mesh, phi), (mesh64, phi64)):
-        ms_.set_density(rho)
-        ms_.set_phi_output(out)
-        ms_.solve()
-        ms_.synchronize()
+    mesh.set_density(rho)
+    mesh.set_phi_output(phi)
+    mesh.solve()
+    mesh.synchronize()
 
-    # accuracy against the FP64 CPU oracle (rank 0) and between the GPU paths
-    acc = {"tolerance": 1e-6}
-    p_split = phi.cpu().numpy()
-    p64 = phi64.cpu().numpy()
-    acc["phi_max_rel_err_split_vs_fp64_gpu"] = float(np.max(np.abs(p_split - p64) / np.abs(p64)))
+    # ---- accuracy of both GPU paths against the FP64 CPU oracle (rank 0), which also gives
+    # the CPU baseline (one whole solve on every host thread; one thread on a slab of shells)
+    acc = {"tolerance_phi": 1e-6, "phi_metric": "max over every cell of |dPhi| / |Phi_oracle|"}
     cpu = None
-    if rank == 0 and world == 1:
-        v, reps, el, cores, ref = cpu_baseline_leg(w, args.cpu_seconds)
-        cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
-               "sample": f"{reps} whole-workload solves (factored FP64 oracle, tables prebuilt) in {el:.1f} s"}
-        acc["phi_max_rel_err_split_vs_oracle"] = float(np.max(np.abs(p_split - ref) / np.abs(ref)))
-        acc["phi_max_rel_err_fp64_gpu_vs_oracle"] = float(np.max(np.abs(p64 - ref) / np.abs(ref)))
+    ref = S = None
+    if with_oracle:
+        from oracle.error_metrics import term_scales
+        log("oracle solve of the whole workload ...")
+        ref, t_all, threads = oracle_reference(w)
+        v1, ns, el1 = oracle_one_thread(w, ref["tables"], t_all, threads)
+        cpu = {"value": 1.0 / t_all, "unit": "solves/s", "cores": threads, "nproc": os.cpu_count(), "kind": "oracle",
+               "sample": f"one whole-workload solve (FP64 oracle, tables prebuilt) on {threads} threads in {t_all:.1f} s",
+               "one_thread": {"value": v1, "unit": "solves/s",
+                              "sample": f"the first {ns} shells on 1 thread in {el1:.2f} s, scaled by shells"}}
+        S = term_scales(w.rho, ref["tables"], m.G)
+        acc["split"] = {"phi_max_rel_err_vs_oracle": phi_error_vs_oracle(phi, ref["phi"]),
+                        **moment_report(mesh, w, ref, S, SPLIT_PRECISION)}
+    mesh64 = phi64 = None
+    if full:
+        phi64 = torch.empty_like(rho)
+        mesh64 = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="fp64", stream=stream)
+        mesh64.set_density(rho)
+        mesh64.set_phi_output(phi64)
+        mesh64.solve()
+        mesh64.synchronize()
+        if with_oracle:
+            acc["fp64_gpu"] = {"phi_max_rel_err_vs_oracle": phi_error_vs_oracle(phi64, ref["phi"]),
+                               **moment_report(mesh64, w, ref, S, "fp64")}
+        acc["phi_max_rel_err_split_vs_fp64_gpu"] = phi_diff_on_device(phi, phi64)
+    ref = S = None
 
-    # ---- timed region: split path, K solves (each one CUDA graph launch of the kernel chain)
+    # ---- timed region: split path, blocks of K solves (each solve one CUDA graph launch)
     for _ in range(args.warmup):
         mesh.solve()
     mesh.synchronize()
@@ -314,24 +687,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        mesh.solve()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
+    t_region = time.perf_counter()
+    times = timed_blocks(mesh.solve, args.steps, args.min_seconds, stream, barrier, max_over_ranks)
+    t_region = time.perf_counter() - t_region
+    clk = clocks.stop(skip_s=0.3)
     mesh.synchronize()
-    local_ms = ev0.elapsed_time(ev1)
+    local_ms = statistics.median(times)
     total_ms = max_over_ranks(local_ms)
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(world, args.steps, total_ms)
 
     # ---- per-kernel durations: the same solves launched kernel by kernel with CUDA events
     # between them on the mesh stream (events cost a little time of their own)
-    kp = max(3, min(args.steps, 1000))
+    kp = max(3, min(args.steps * 5, 200))
     mesh.profile(True)
     for _ in range(kp):
         mesh.solve()
@@ -339,106 +707,83 @@ def run_ours(args):
     mesh.profile(False)
     prof_ms_per_step = sum(v["total_ms"] for v in prof.values()) / kp
 
-    # ---- float64 GPU path on the same workload
-    k64 = max(3, min(args.steps // 50, 200))
-    for _ in range(2):
-        mesh64.solve()
-    mesh64.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(k64):
-        mesh64.solve()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms64 = max_over_ranks(e0.elapsed_time(e1)) / k64
-    mesh64.synchronize()
+    line_extra = {}
+    if full:
+        # ---- float64 GPU path on the same density, at least 20 solves
+        k64 = 20
+        for _ in range(2):
+            mesh64.solve()
+        mesh64.synchronize()
+        t64 = timed_blocks(mesh64.solve, k64, 0.0, stream, barrier, max_over_ranks)
+        ms64 = max_over_ranks(statistics.median(t64)) / k64
+        mesh64.synchronize()
+        mesh64.close()
+        del phi64
+        torch.cuda.empty_cache()
+        line_extra["fp64_gpu"] = {"solves_per_s": world / (ms64 * 1e-3), "ms_per_solve": ms64, "steps": k64,
+                                  "blocks": len(t64), "gcell_mode_per_s": world / (ms64 * 1e-3) * cells * KL / 1e9}
+        line_extra["speedup_split_vs_fp64_gpu"] = ms64 / ms_per_step
 
-    # ---- end to end through the C ABI with pinned host buffers
-    rho_h = torch.from_numpy(w.rho).pin_memory()
-    phi_h = torch.empty_like(rho_h).pin_memory()
-    ke = max(3, min(args.steps // 100, 100))
-    mesh.solve_host_ptr(rho_h.data_ptr(), phi_h.data_ptr())
-    barrier()
-    t0 = time.perf_counter()
-    # each step uploads its density and downloads its potential; consecutive steps
-    # overlap one download with the next upload, and the clock stops at the last copy
-    for _ in range(ke):
-        mesh.solve_host_ptr_async(rho_h.data_ptr(), phi_h.data_ptr())
-    mesh.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_err = float(np.max(np.abs(phi_h.numpy() - p_split)))
+        # ---- end to end through the C ABI with pinned host buffers: every step uploads its
+        # density and downloads its potential; consecutive steps overlap one download with the
+        # next upload, and the clock stops at the last copy
+        rho_h = torch.from_numpy(w.rho).pin_memory()
+        w.rho = None
+        phi_h = torch.empty_like(rho_h).pin_memory()
+        mesh.solve_host_ptr(rho_h.data_ptr(), phi_h.data_ptr())
+        t0 = time.perf_counter()
+        mesh.solve_host_ptr(rho_h.data_ptr(), phi_h.data_ptr())
+        one = time.perf_counter() - t0
+        ke = max(20, min(5000, int(math.ceil(1.0 / max(one, 1e-6)))))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            mesh.solve_host_ptr_async(rho_h.data_ptr(), phi_h.data_ptr())
+        mesh.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e_err = float((phi_h.view(-1)[:1 << 24].cuda() - phi.view(-1)[:1 << 24]).abs().max().item())
+        line_extra["e2e"] = {"value": world * ke / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * cells,
+                             "d2h_bytes_per_step": 8 * cells, "steps": ke,
+                             "max_abs_diff_vs_device_solve_first_16M_cells": e2e_err,
+                             "api": "mp_solve_host_async, pinned host buffers, host clock"}
+        del rho_h, phi_h
+    mesh.close()
+    del rho, phi
+    w = None
+    torch.cuda.empty_cache()
 
     rates = mpl.probe_rates()
+    if full:
+        line_extra["other_workloads"] = {}
+        for name in [n for n in ("presn", "lognormal", "spheroid") if n != args.workload]:
+            log(f"side workload {name} ...")
+            line_extra["other_workloads"][name] = side_workload(name, args, stream, with_oracle, hbm_peak)
+        log("batch workload ...")
+        line_extra["other_workloads"]["batch"] = batch_workload(args, stream, with_oracle, hbm_peak)
+        gravity, coarsen = beside_solve(stream, hbm_peak, rates, args.steps)
+        line_extra["gravity_sources"] = gravity
+        line_extra["coarsen_blocks"] = coarsen
 
-    # ---- gravitational source terms (Sec. 3) of this solve's potential: momentum S and
-    # energy E from a synthetic velocity; float64, bound by the float64 pipe
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(7)
-    gvel = torch.randn(3 * cells, dtype=torch.float64, device="cuda", generator=gen)
-    gS = torch.empty(3 * cells, dtype=torch.float64, device="cuda")
-    gE = torch.empty(cells, dtype=torch.float64, device="cuda")
-    kg = max(3, min(args.steps // 200, 50))
-    for _ in range(2):
-        mesh.gravity_sources(v=gvel, S=gS, E=gE)
-    mesh.synchronize()
-    e0.record(stream)
-    for _ in range(kg):
-        mesh.gravity_sources(v=gvel, S=gS, E=gE)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    g_us = max_over_ranks(e0.elapsed_time(e1)) / kg * 1e3
-    fp64_instr_peak = rates["fp64_tflops"] * 1e12 / 2.0  # one FMA instruction = 2 flops
-    gravity = {"kernel": "gravity_sources", "launches": kg, "avg_launch_us": g_us,
-               "algorithmic_bytes_per_cell": 72, "hbm_gbs": 72 * cells / g_us / 1e3,
-               "hbm_frac": 72 * cells / g_us / 1e3 / measured_peaks()[0],
-               "fp64_instr_per_cell": 12, "fp64_instr_per_s": 12 * cells / (g_us * 1e-6),
-               "fp64_frac": 12 * cells / (g_us * 1e-6) / fp64_instr_peak, "bound": "fp64",
-               "note": "S [3] and E from Phi, rho, v [3]: 9 float64 reads + 4 writes per cell"}
-    del gvel, gS, gE
-
-    # ---- coarsening-block averaging (Sec. 2.1 / 2.3) on the paper's standard dimensionless
-    # mesh (N_theta = 256, r_core = 0.25, R_radial = 3.68, N_phi = 2 N_theta), one field in place
-    pm = W.paper_mesh(256, 0.25, 3.68, 0, 3)
-    cmesh = mpl.Mesh(pm.r, pm.theta, pm.phi, 2, 1.0, precision="fp64", stream=stream)
-    c_t, c_p = cmesh.coarsening_factors()
-    n_pm = (pm.r.size - 1) * (pm.theta.size - 1) * (pm.phi.size - 1)
-    coarse_cells = int(((c_t[:, None] > 1) | (c_p > 1)).sum()) * (pm.phi.size - 1)
-    cfield = torch.randn(n_pm, dtype=torch.float64, device="cuda", generator=gen)
-    kc = max(3, min(args.steps // 200, 50))
-    for _ in range(2):
-        cmesh.coarsen(cfield)
-    cmesh.synchronize()
-    e0.record(stream)
-    for _ in range(kc):
-        cmesh.coarsen(cfield)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    c_us = max_over_ranks(e0.elapsed_time(e1)) / kc * 1e3
-    coarsen = {"kernel": "coarsen_blocks", "mesh": "paper rule N_theta = 256: 942 x 256 x 512",
-               "cells": n_pm, "coarsened_cells": coarse_cells, "launches": kc, "avg_launch_us": c_us,
-               "algorithmic_bytes": 16 * coarse_cells, "hbm_gbs": 16 * coarse_cells / c_us / 1e3,
-               "hbm_frac": 16 * coarse_cells / c_us / 1e3 / measured_peaks()[0], "bound": "fp64",
-               "note": "every coarsened cell read once and written once (in place); the float64 pipe "
-                       "(about 1.6 float64 instructions a coarsened cell) bounds it before HBM"}
-    cmesh.close()
-    del cfield
-
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel, whole-step roofline, tensor-pipe fractions
     log("kernels:", json.dumps(prof))
     dom = max(prof, key=lambda k: prof[k]["total_ms"])
     avg_ms = prof[dom]["total_ms"] / prof[dom]["launches"]
     nbytes = alg_bytes(dom, cells, rows, m.shape[0], m.L, KL)
-    peak, peak_kind = measured_peaks()
     achieved = nbytes / (avg_ms * 1e-3) / 1e9
     traffic = None
-    rec = NCU_TRAFFIC.get(dom) if args.workload == "presn" else None  # the record is for that workload
+    rec = NCU_TRAFFIC.get((args.workload, dom))
     if rec and rec[2] == source_hash(rec[1]):
         traffic = rec[0]
     kernels = {k: {"launches": v["launches"], "avg_us": 1e3 * v["total_ms"] / v["launches"],
                    "share": v["total_ms"] / sum(x["total_ms"] for x in prof.values())} for k, v in prof.items()}
+    tensor = {}
+    for k in ("split_phi_project_tc", "split_synth_tc"):
+        if k in prof:
+            useful, executed = mma_flops(k, m.shape, m.L, 3)
+            t = prof[k]["total_ms"] / prof[k]["launches"] * 1e-3
+            tensor[k] = {"executed_tflops": executed / t / 1e12, "useful_tflops": useful / t / 1e12,
+                         "peak_tflops": tc_peak, "frac": executed / t / 1e12 / tc_peak,
+                         "hbm_gbs": 8 * cells / t / 1e9, "hbm_frac": 8 * cells / t / 1e9 / hbm_peak}
 
     if rank == 0:
         line = {
@@ -447,37 +792,32 @@ def run_ours(args):
             "vs_baseline": None, "dtype": SPLIT_PRECISION, "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "cells": cells, "l_max": m.L, "moments": KL,
                        "precision": SPLIT_PRECISION, "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2 (rho {8 * cells / 1e6:.0f} MB + Phi {8 * cells / 1e6:.0f} MB per step)"},
+                       "l2": f"inputs larger than L2 (rho {8 * cells / 1e6:.0f} MB + Phi {8 * cells / 1e6:.0f} MB per step)",
+                       "timing": f"{len(times)} blocks of {args.steps} solves ({t_region:.2f} s), median block / steps"},
             "gcell_mode_per_s": value * cells * KL / 1e9,
-            "fp64_gpu": {"solves_per_s": world / (ms64 * 1e-3), "ms_per_solve": ms64, "steps": k64,
-                         "gcell_mode_per_s": world / (ms64 * 1e-3) * cells * KL / 1e9},
-            "speedup_split_vs_fp64_gpu": ms64 / ms_per_step,
             "accuracy": acc,
-            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
                          "algorithmic_bytes": nbytes, "avg_launch_us": avg_ms * 1e3},
+            "roofline_step": {"algorithmic_bytes": 16 * cells, "achieved_gbs": 16 * cells / (ms_per_step * 1e-3) / 1e9,
+                              "frac": 16 * cells / (ms_per_step * 1e-3) / 1e9 / hbm_peak,
+                              "note": "rho read once + Phi written once per solve (16 B/cell), whole solve"},
+            "tensor_pipe": tensor,
             "kernels": kernels,
             "kernels_note": f"per-kernel CUDA-event durations from {kp} separately profiled solves "
                             f"(sum {prof_ms_per_step * 1e3:.1f} us/solve)",
-            "e2e": {"value": world * ke / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * cells,
-                    "d2h_bytes_per_step": 8 * cells, "steps": ke, "max_abs_diff_vs_device_solve": e2e_err},
-            # kernels of the split chain per solve (one graph launch each) x timed solves
-            "gpu_launches": len(prof) * args.steps,
-            "gravity_sources": gravity,
-            "coarsen_blocks": coarsen,
+            "gpu_launches": len(prof) * args.steps * len(times),
             "device_rates": {"fp64_tflops_measured": rates["fp64_tflops"],
                              "cvt_f64_to_f32_per_s_measured": rates["cvt_f64_f32_per_s"]},
             "clocks": clk,
         }
+        line.update(line_extra)
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
-    mesh.close()
-    mesh64.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
-
 
 def main():
     args = parse_args()

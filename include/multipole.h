@@ -192,6 +192,20 @@ MP_API mp_status mp_solve_host_async(mp_mesh *mesh, const double *rho_host, doub
 MP_API mp_status mp_mesh_synchronize(mp_mesh *mesh);
 
 /*
+ * Failure detection: every wait inside the split-precision kernels (on a copy,
+ * an MMA or another warp role of the same block) is bounded.  When one runs past
+ * the budget the block records MP_ERR_TIMEOUT in the mesh's device error word,
+ * lets every copy and MMA it issued finish (with the full default budget), frees
+ * its tensor memory and exits; mp_mesh_synchronize() then returns
+ * MP_ERR_TIMEOUT and the mesh stays usable.  This sets that budget in SM clock
+ * cycles for later solves of the mesh; cycles <= 0 restores the default of
+ * 2e9 cycles (about a second at the boost clock).  A tiny budget makes the
+ * waits run out on purpose, which is how the abort path is tested.  The paper
+ * has no counterpart.  Waits for the mesh's stream first; blocks until set.
+ */
+MP_API mp_status mp_set_wait_budget(mp_mesh *mesh, long long cycles);
+
+/*
  * Per-kernel timing on the mesh's stream (CUDA events around each launch).
  * mp_profile_enable(mesh, 1) starts recording (and resets totals);
  * mp_profile_read() waits for the stream, then fills up to cap entries with

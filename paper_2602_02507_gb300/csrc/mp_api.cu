@@ -440,7 +440,7 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
     ALLOC(m->d_MR, (size_t)(n_r + 1) * m->KL);
     ALLOC(m->d_MI, (size_t)(n_r + 1) * m->KL);
     ALLOC(m->d_C, (size_t)n_r * m->KL);
-    ALLOC(m->d_err, 1);
+    ALLOC(m->d_err, 4);  // [0] error word, [2..3] budget of the pipeline waits (int64, 0: default)
     if (m->eff_prec == MP_PREC_FP64) {
         ALLOC(m->d_F64, (size_t)m->R * m->P);
         ALLOC(m->d_G64, (size_t)m->R * m->P);
@@ -483,7 +483,7 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
                                          m->stream),
                          "copy edges");
         if (st != MP_OK) return fail(st);
-        st = cuda_status(cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream), "clear error word");
+        st = cuda_status(cudaMemsetAsync(m->d_err, 0, 4 * sizeof(int), m->stream), "clear error word");
         if (st != MP_OK) return fail(st);
         st = cuda_status(launch_tables(m), "build tables");
         if (st != MP_OK) return fail(st);
@@ -659,6 +659,16 @@ mp_status mp_mesh_synchronize(mp_mesh *m)
         if (err & DEV_ERR_NONFINITE) return set_error(MP_ERR_NONFINITE, "density holds NaN or infinity");
         return set_error(MP_ERR_CUDA, "device error word %d", err);
     }
+    return MP_OK;
+}
+
+mp_status mp_set_wait_budget(mp_mesh *m, long long cycles)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard dg(m->device);
+    const long long v = cycles > 0 ? cycles : 0;
+    MP_TRY(cudaStreamSynchronize(m->stream));
+    MP_TRY(cudaMemcpy(m->d_err + 2, &v, sizeof(v), cudaMemcpyHostToDevice));
     return MP_OK;
 }
 

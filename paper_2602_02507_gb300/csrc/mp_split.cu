@@ -70,7 +70,28 @@ struct Ring {
             phase ^= 1u;
         }
     }
+    __device__ __forceinline__ void prev(int n)
+    {
+        if (idx == 0) {
+            idx = n;
+            phase ^= 1u;
+        }
+        --idx;
+    }
 };
+
+// After an abort: waits (bounded by the full budget) for the last min(n, issued) copies
+// issued into the n-slot ring whose next free position is r, so that none of them is still
+// writing into this block's shared memory when the block exits.
+__device__ __forceinline__ void drain_ring(uint64_t *full, Ring r, int n, int issued)
+{
+    for (int k = 0; k < n && k < issued; ++k) {
+        r.prev(n);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(smem_u32(&full[r.idx]), r.phase) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
+        }
+    }
+}
 
 // Chunk order of a tile: a rotation by a tile-dependent offset, so that the SMs
 // streaming different tiles address different parts of their rows at any moment
@@ -193,7 +214,10 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                     if (two) tma_load_2d_hint(dst + BOX_BYTES, &tmS, fb, kc * BK + 16, tile * kBM, l2_first);
                     ++issued;
                     if (prm.b_resident) continue;
-                    if (!mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err)) break;
+                    if (!mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err)) {
+                        rs.next(NS_S);  // the density stage was issued: the drain counts back from past it
+                        break;
+                    }
                     const uint32_t bb = smem_u32(&b_full[rb.idx]);
                     mbar_arrive_expect_tx(bb, prm.bload);
                     bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bload), prm.tabB + (size_t)kc * prm.bchunk,
@@ -202,31 +226,17 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                     rb.next(NS_B);
                 }
             }
-            if (*abort_flag && issued > 0) {
-                // drain copies still in flight into this CTA's shared memory
-                Ring back = rs;
-                for (int n = 0; n < NS_S && n < issued; ++n) {
-                    back.idx = (back.idx == 0) ? NS_S - 1 : back.idx - 1;
-                    if (back.idx == NS_S - 1) back.phase ^= 1u;
+            // Every copy this thread issued has landed before the CTA can exit (another role may
+            // abort after this loop ends; without an abort the phases are long complete).
+            drain_ring(s_full, rs, NS_S, issued);
+            if (prm.b_resident) {
+                if ((int)blockIdx.x < prm.n_tiles) {
                     const long long t0 = clock64();
-                    while (!mbar_try_wait(smem_u32(&s_full[back.idx]), back.phase) &&
-                           clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
+                    while (!mbar_try_wait(smem_u32(&b_full[0]), 0) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
                     }
                 }
-                Ring bback = rb;
-                for (int n = 0; n < NS_B && n < issued_b; ++n) {
-                    bback.idx = (bback.idx == 0) ? NS_B - 1 : bback.idx - 1;
-                    if (bback.idx == NS_B - 1) bback.phase ^= 1u;
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait(smem_u32(&b_full[bback.idx]), bback.phase) &&
-                           clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
-                    }
-                }
-            }
-            if (*abort_flag && prm.b_resident) {
-                const long long t0 = clock64();
-                while (!mbar_try_wait(smem_u32(&b_full[0]), 0) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
-                }
+            } else {
+                drain_ring(b_full, rb, NS_B, issued_b);
             }
         }
     } else if (warp == 1) {
@@ -865,6 +875,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
             }
             pdl_wait();
             Ring ra, rb;
+            int issued_a = 0, issued_b = 0;
             for (int unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x, ra.next(NS_A)) {
                 const int tile = unit / prm.n_nc, nc = unit - tile * prm.n_nc;
                 ok = mbar_wait(smem_u32(&a_empty[ra.idx]), ra.phase ^ 1, abort_flag, prm.err);
@@ -874,6 +885,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                 mbar_arrive_expect_tx(fb, a_stage);
                 bulk_load(smem_u32(dst), prm.Aop + (size_t)tile * prm.a_bytes, prm.a_bytes, fb);
                 bulk_load(smem_u32(dst + prm.a_bytes), prm.G0 + (size_t)tile * 256, 1024, fb);
+                ++issued_a;
                 if (!prm.b_resident) {
                     for (int c = nc * nkk; c < (nc + 1) * nkk && ok; ++c, rb.next(NS_B)) {
                         ok = mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err);
@@ -881,14 +893,22 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                         mbar_arrive_expect_tx(smem_u32(&b_full[rb.idx]), prm.bchunk);
                         bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bchunk), prm.tabT + (size_t)c * prm.bchunk,
                                   prm.bchunk, smem_u32(&b_full[rb.idx]));
+                        ++issued_b;
                     }
                 }
             }
-            if (*abort_flag) {
-                // let copies already issued into this CTA's shared memory land (bounded)
-                const long long t0 = clock64();
-                while (clock64() - t0 < 100000) {
+            // Every copy this thread issued has landed before the CTA can exit: another role may
+            // abort after this loop ends, leaving stages nobody waits for.  In a run without an
+            // abort these waits find the phases long complete.
+            drain_ring(a_full, ra, NS_A, issued_a);
+            if (prm.b_resident) {
+                if (blockIdx.x < n_units) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(smem_u32(&b_full[0]), 0) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
+                    }
                 }
+            } else {
+                drain_ring(b_full, rb, NS_B, issued_b);
             }
         }
     } else if (warp == 1) {

@@ -60,14 +60,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 // Bounded wait.  Returns false (after raising the CTA's abort flag and the
 // mesh error word) when the phase does not complete within the budget, or
 // when another role of the CTA already aborted.
+// The mesh's device error word is err[0]; err[2..3] hold, as one 64-bit value, the
+// budget of these pipeline waits in SM clock cycles (0 or less: MP_WAIT_BUDGET_CYCLES;
+// mp_set_wait_budget changes it).  The drains that follow an abort always keep the
+// full compile-time budget, so that no copy or MMA outlives the block that issued it.
+__device__ __forceinline__ long long wait_budget(const int *err)
+{
+    const long long b = *reinterpret_cast<const volatile long long *>(err + 2);
+    return b > 0 ? b : MP_WAIT_BUDGET_CYCLES;
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
+    const long long budget = wait_budget(err);
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > MP_WAIT_BUDGET_CYCLES) {
+        if (clock64() - t0 > budget) {
             *abort_flag = 1;
             atomicOr(err, DEV_ERR_TIMEOUT);
             return false;

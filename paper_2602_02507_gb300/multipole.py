@@ -62,6 +62,7 @@ def load_library(path: str = LIB_PATH):
         "mp_solve_host": [vp, vp, vp],
         "mp_solve_host_async": [vp, vp, vp],
         "mp_mesh_synchronize": [vp],
+        "mp_set_wait_budget": [vp, ctypes.c_longlong],
         "mp_profile_enable": [vp, i],
         "mp_profile_read": [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i), dp, i, ctypes.POINTER(i)],
         "mp_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(vp)],
@@ -243,6 +244,10 @@ class Mesh:
 
     def synchronize(self):
         _check(self._lib.mp_mesh_synchronize(self._h), "mp_mesh_synchronize")
+
+    def set_wait_budget(self, cycles: int):
+        """Budget of the device-side pipeline waits in SM clock cycles (0: the default)."""
+        _check(self._lib.mp_set_wait_budget(self._h, int(cycles)), "mp_set_wait_budget")
 
     def solve_host(self, rho_host: np.ndarray, phi_host: np.ndarray):
         """End-to-end solve from host arrays (float64, rho layout; pinned is fastest)."""

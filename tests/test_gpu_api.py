@@ -34,6 +34,41 @@ def test_nonfinite_density_is_reported(prec):
         mesh.synchronize()  # the error word was cleared
 
 
+@pytest.mark.parametrize("shape,L", [((8, 16, 32), 4), ((64, 32, 64), 8)])
+def test_expired_device_wait_reports_timeout_and_the_mesh_recovers(shape, L):
+    """Failure detection without a fault: a wait budget of one clock cycle makes the
+    bounded pipeline waits of the split kernels run out.  Every block then raises its
+    abort flag, lets the copies and MMAs it issued finish, frees its tensor memory and
+    exits; mp_mesh_synchronize reports MP_ERR_TIMEOUT.  With the default budget back,
+    the same mesh solves correctly again."""
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = W.presn(n_r=shape[0], n_theta=shape[1], n_phi=shape[2], L=L, r_lo=1e7, r_hi=3e7)
+    m = w.mesh
+    ref = oracle_solve(w)["phi"]
+    rho = torch.from_numpy(w.rho).cuda()
+    phi = torch.empty_like(rho)
+    with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3") as mesh:
+        assert mesh.info()["effective_precision"] == 1
+        mesh.set_density(rho)
+        mesh.set_phi_output(phi)
+        mesh.solve()
+        mesh.synchronize()
+        mesh.set_wait_budget(1)
+        for _ in range(2):  # graph replay and the eager (profiled) launches
+            mesh.solve()
+            with pytest.raises(mpl.MultipoleError) as ei:
+                mesh.synchronize()
+            assert ei.value.name == "MP_ERR_TIMEOUT"
+            mesh.profile(True)
+        mesh.profile(False)
+        mesh.set_wait_budget(0)
+        phi.fill_(0.0)
+        mesh.solve()
+        mesh.synchronize()
+        assert phi_rel_err(phi.cpu().numpy(), ref) <= 1e-6
+
+
 def test_solve_without_density_is_not_ready():
     from paper_2602_02507_gb300 import multipole as mpl
     w = W.presn(n_r=4, n_theta=8, n_phi=16, L=2, materialize=False)

@@ -13,7 +13,8 @@ printed for the record.
 import numpy as np
 import pytest
 
-from gpu_helpers import per_l_errors, phi_rel_err
+from gpu_helpers import (edge_term_errors, moment_term_errors, per_l_errors, phi_rel_err, split_moment_bar,
+                         term_scales)
 from paper_2602_02507_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -29,7 +30,7 @@ def _built():
 
 
 def _solve(w, prec, rho_dev=None, shells=None):
-    """Phi (whole mesh, or the listed shells) and the angular moments of one GPU solve."""
+    """Phi (whole mesh, or the listed shells), the angular and edge moments of one GPU solve."""
     import torch
     from paper_2602_02507_gb300 import multipole as mpl
     m = w.mesh
@@ -37,48 +38,78 @@ def _solve(w, prec, rho_dev=None, shells=None):
     phi = torch.empty_like(rho)
     n_r, K = m.shape[0], m.KL
     A = torch.empty(n_r * K, dtype=torch.float64, device="cuda")
+    MR = torch.empty((n_r + 1) * K, dtype=torch.float64, device="cuda")
+    MI = torch.empty((n_r + 1) * K, dtype=torch.float64, device="cuda")
     with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=prec) as mesh:
         mesh.set_density(rho)
         mesh.set_phi_output(phi)
         mesh.solve()
-        mesh.get_moments(A, None, None)
+        mesh.get_moments(A, MR, MI)
         mesh.synchronize()
         eff = mesh.info()["effective_precision"]
-    out = phi if shells is None else phi[shells]
-    return out.cpu().numpy(), A.cpu().numpy().reshape(n_r, K), eff
+    out = phi.view(n_r, -1) if shells is None else phi.view(n_r, -1)[shells]
+    mom = {"A": A.cpu().numpy().reshape(n_r, K), "MR": MR.cpu().numpy().reshape(n_r + 1, K),
+           "MI": MI.cpu().numpy().reshape(n_r + 1, K)}
+    return out.cpu().numpy().reshape(-1 if shells is None else len(shells), *m.shape[1:]), mom, eff
+
+
+def _check_moments(tag, w, prec, mom, ref, S, L):
+    """Per-degree moment errors of a split solve against the error model's bar; float64
+    solves against 1e-12 of the same term scale."""
+    bar = split_moment_bar(w.mesh, prec) if prec != "fp64" else 1e-12
+    eA = moment_term_errors(mom["A"], ref["A"], S, L)
+    eM = edge_term_errors(mom, ref, S)
+    print(f"{tag} {prec}: per-l A/S max {max(eA):.2e}, M^R {max(eM['MR']):.2e}, M^I {max(eM['MI']):.2e} "
+          f"(bar {bar:.2e})")
+    assert max(eA) <= bar, (prec, eA)
+    assert max(eM["MR"]) <= bar, (prec, eM["MR"])
+    assert max(eM["MI"]) <= bar, (prec, eM["MI"])
 
 
 def test_lognormal_full_size_1024x256x512_L32():
     from oracle import oracle as O
     w = W.lognormal()
     m = w.mesh
-    ref = O.solve(O.build_tables(m.r, m.theta, m.phi, m.L), w.rho, m.G)
+    tab = O.build_tables(m.r, m.theta, m.phi, m.L)
+    ref = O.solve(tab, w.rho, m.G)
+    ref["tables"] = tab
+    S = term_scales(w.rho, tab, m.G)
     for prec, tol in (("fp64", 1e-12), ("bf16x3", 1e-6), ("bf16x6", 1e-6)):
-        phi, A, eff = _solve(w, prec)
+        phi, mom, eff = _solve(w, prec)
         assert eff == {"fp64": 0, "bf16x3": 1, "bf16x6": 2}[prec]
         err = phi_rel_err(phi, ref["phi"])
-        print(f"lognormal {prec}: phi {err:.3e}, per-l A max {max(per_l_errors(A, ref['A'], m.L)):.3e}")
+        print(f"lognormal {prec}: phi {err:.3e}, per-l A vs degree max {max(per_l_errors(mom['A'], ref['A'], m.L)):.3e}")
         assert err <= tol, (prec, err)
+        _check_moments("lognormal", w, prec, mom, ref, S, m.L)
+
+
+LARGE_SHELLS = sorted(set([0, 1, 2046, 2047] + list(range(0, 2048, 32))))
 
 
 def test_large_full_size_2048x512x1024_L64_sampled_shells():
+    """Every moment of the whole mesh against the oracle; Phi on every 32nd shell plus the
+    first and last two (68 of 2048 shells, 35.7 M cells)."""
     from oracle import oracle as O
     w = W.large(materialize=True)
     m = w.mesh
     tab = O.build_tables(m.r, m.theta, m.phi, m.L)
     ref = O.solve(tab, w.rho, m.G, want_phi=False)
-    shells = [0, 1, 700, 1400, 2046, 2047]
+    ref["tables"] = tab
+    S = term_scales(w.rho, tab, m.G)
+    shells = LARGE_SHELLS
     ref_phi = O.potential_shells(tab, ref["C"], shells)
     import torch
     rho = torch.from_numpy(w.rho).cuda()
     del w
     for prec in ("fp64", "bf16x3"):
-        phi, A, _ = _solve(W.large(), prec, rho_dev=rho, shells=shells)
+        phi, mom, _ = _solve(W.large(), prec, rho_dev=rho, shells=shells)
         pointwise = phi_rel_err(phi, ref_phi)
         maxnorm = float(np.abs(phi - ref_phi).max() / np.abs(ref_phi).max())
+        A = mom["A"]
         mono = float(np.max(np.abs(A[:, 0] - ref["A"][:, 0]) / np.abs(ref["A"][:, 0])))
         print(f"large {prec}: phi pointwise {pointwise:.3e}, max-norm {maxnorm:.3e}, A_00 {mono:.3e}")
         assert pointwise <= (1e-12 if prec == "fp64" else 1e-6), (prec, pointwise, maxnorm, mono)
+        _check_moments("large", W.large(), prec, mom, ref, S, m.L)
         torch.cuda.empty_cache()
 
 
@@ -109,9 +140,15 @@ def test_batch_of_64_uneven_meshes():
         meshes[n].synchronize()
         assert np.array_equal(phis[n].cpu().numpy(), batch_phi[n]), n
     b.close()
-    # the smallest instances against the oracle
+    # against the oracle: the three smallest instances, and the smallest instance of each
+    # l_max value (8, 16, 32)
     order = sorted(range(len(draws)), key=lambda n: np.prod(draws[n][0]) * draws[n][1])
-    for n in order[:3]:
+    picks = list(order[:3])
+    for L in sorted({d[1] for d in draws}):
+        n = min((k for k in range(len(draws)) if draws[k][1] == L), key=lambda k: np.prod(draws[k][0]))
+        if n not in picks:
+            picks.append(n)
+    for n in picks:
         w = W.batch_instance(n, draws)
         m = w.mesh
         ref = O.solve(O.build_tables(m.r, m.theta, m.phi, m.L), w.rho, m.G)
