@@ -80,6 +80,8 @@ def parse_args():
                    help="mesh and density of the headline (large is the benchmarked configuration)")
     p.add_argument("--min-seconds", type=float, default=1.0, help="device time the timed blocks fill")
     p.add_argument("--lean", action="store_true", help="split path timing only (profiler runs)")
+    p.add_argument("--theta-engine", choices=["auto", "tensor", "cuda"], default="auto",
+                   help="theta stages of the split path (auto: the mesh's default)")
     return p.parse_args()
 
 
@@ -642,6 +644,7 @@ def run_ours(args):
     rho = torch.from_numpy(w.rho).cuda()
     phi = torch.empty_like(rho)
     mesh = mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=SPLIT_PRECISION, stream=stream)
+    mesh.set_theta_engine(args.theta_engine)
     mesh.set_density(rho)
     mesh.set_phi_output(phi)
     mesh.solve()
@@ -747,6 +750,7 @@ def run_ours(args):
                              "max_abs_diff_vs_device_solve_first_16M_cells": e2e_err,
                              "api": "mp_solve_host_async, pinned host buffers, host clock"}
         del rho_h, phi_h
+    theta_tc = bool(mesh.info()["theta_tensor_cores"])
     mesh.close()
     del rho, phi
     w = None
@@ -792,6 +796,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": SPLIT_PRECISION, "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "cells": cells, "l_max": m.L, "moments": KL,
                        "precision": SPLIT_PRECISION, "parallelism": f"replicas x{world}",
+                       "theta_stages": "tensor cores (tcgen05), m >= 1" if theta_tc else "CUDA cores",
                        "l2": f"inputs larger than L2 (rho {8 * cells / 1e6:.0f} MB + Phi {8 * cells / 1e6:.0f} MB per step)",
                        "timing": f"{len(times)} blocks of {args.steps} solves ({t_region:.2f} s), median block / steps"},
             "gcell_mode_per_s": value * cells * KL / 1e9,

@@ -97,6 +97,8 @@ typedef struct {
     size_t device_bytes;     /* device memory the mesh holds (tables + workspace)    */
     int tuned_candidates;    /* configurations the last mp_autotune timed (0: none,  */
                              /* or the choice came from the cache file)              */
+    int theta_tensor_cores;  /* 1: the split path runs the theta stages of the       */
+                             /* orders m >= 1 on the tensor cores (tcgen05)          */
 } mp_mesh_info;
 
 /*
@@ -192,6 +194,20 @@ MP_API mp_status mp_solve_host_async(mp_mesh *mesh, const double *rho_host, doub
 MP_API mp_status mp_mesh_synchronize(mp_mesh *mesh);
 
 /*
+ * Engine of the theta factors of both angular contractions on the split path
+ * (Eq. (AngularMomentsDiscrete) and Eq. (Solution), the sums over polar cells and
+ * over degrees): 1 runs the orders m >= 1 as split-bf16 tcgen05 GEMMs, one per order
+ * (the m = 0 column stays on CUDA cores in compensated float32 / double-float);
+ * 2 runs every order on CUDA cores in float32; 0 restores the mesh's default (the
+ * tensor cores where the CUDA-core kernels cannot keep their tables in shared memory).
+ * mp_autotune also times both.  Both give results within the split-path tolerance;
+ * they differ in rounding.  Waits for the mesh's stream; later solves re-capture
+ * their graph.  Errors: MP_ERR_INVALID_ARG (engine outside 0..2), MP_ERR_UNSUPPORTED
+ * (1 on a float64 mesh, or l_max = 0).
+ */
+MP_API mp_status mp_set_theta_engine(mp_mesh *mesh, int engine);
+
+/*
  * Failure detection: every wait inside the split-precision kernels (on a copy,
  * an MMA or another warp role of the same block) is bounded.  When one runs past
  * the budget the block records MP_ERR_TIMEOUT in the mesh's device error word,
@@ -229,9 +245,10 @@ MP_API mp_status mp_batch_destroy(mp_batch *batch);
 
 /*
  * Pick launch parameters for the mesh by timing candidates on the device
- * (needs a bound density): the projection's density ring depth, the
- * synthesis table ring depth (when the table is not resident) and the threads
- * per moment column of the radial recurrences.  The choice is cached in
+ * (needs a bound density): the projection's density ring depth and table
+ * residency, the synthesis table ring depth (when the table is not resident),
+ * the threads per moment column of the radial recurrences and the engine of the
+ * theta stages (tensor cores or CUDA cores, see mp_set_theta_engine).  The choice is cached in
  * cache_path (a text file, may be NULL) keyed by (n_r, n_theta, n_phi, l_max,
  * precision) and reused by later meshes of the same key.
  */

@@ -119,23 +119,32 @@ def edge_term_errors(got, ref, S):
 
 def split_moment_bar(mesh, precision):
     """Bound of the split path's moment errors relative to the term scale S, from its
-    error model.  The phi projection multiplies density deviations (x - x_ref, split into
-    2 bf16 terms for BF16X3, 3 for BF16X6) by the table (3 bf16 terms): the dropped low
-    products and split residuals leave 3 * 2^-18 (BF16X3) or 5 * 2^-27 (BF16X6) of each
-    |term|, doubled because |x - x_ref| <= |x| + |x_ref|.  The tensor core adds each MMA's
-    products into a float32 accumulator with truncation: at most 2^-23 of the running sum
-    per MMA, over chains of 2 * NPROD * ceil(n_kc / nacc) MMAs (32 azimuthal cells per K
-    chunk, chunks dealt over nacc accumulators).  The theta contraction in float32 with
-    compensated sums adds about 3 * 2^-24.  The bar is twice the sum."""
-    n_p = mesh.shape[2]
+    error model.  Both factors of step (a) are bf16 products with float32 accumulation on
+    the tensor cores:
+    - the phi projection multiplies density deviations (x - x_ref, split into 2 bf16
+      terms for BF16X3, 3 for BF16X6) by the table (3 bf16 terms): the dropped low
+      products and split residuals leave 3 * 2^-18 (BF16X3) or 5 * 2^-27 (BF16X6) of each
+      |term|, doubled because |x - x_ref| <= |x| + |x_ref|; the accumulator adds each
+      MMA's products with truncation, at most 2^-23 of the running sum per MMA, over
+      chains of 2 * NPROD * ceil(n_kc / nacc) MMAs (32 azimuthal cells per K chunk, chunks
+      dealt over nacc accumulators);
+    - the theta contraction of the orders m >= 1 splits F the same way (its split error
+      once more) over chains of 2 * NPROD * ceil(n_kc_theta / nacc_theta) MMAs (32 polar
+      cells per chunk); the m = 0 column, in compensated float32, adds about 3 * 2^-24.
+    The bar is twice the sum."""
+    n_r, n_t, n_p = mesh.shape
     L = mesh.L
     x6 = precision == "bf16x6"
     nprod = 6 if x6 else 3
+    eps_term = 5 * 2.0 ** -27 if x6 else 3 * 2.0 ** -18
     npad = -(-(2 * L + 1) // 16) * 16
     n_kc = -(-n_p // 32)
     nacc = max(1, min(4, 256 // npad, n_kc))
-    chain = 2 * nprod * (-(-n_kc // nacc))
-    eps_split = 2.0 * (5 * 2.0 ** -27 if x6 else 3 * 2.0 ** -18)
-    eps_acc = chain * 2.0 ** -23
+    eps_proj = 2.0 * eps_term + 2 * nprod * (-(-n_kc // nacc)) * 2.0 ** -23
     eps_theta = 3 * 2.0 ** -24
-    return 2.0 * (eps_split + eps_acc + eps_theta)
+    if L >= 1:
+        nmax = -(-L // 16) * 16
+        n_kct = -(-n_t // 32)
+        nacct = max(1, min(4, 256 // nmax, n_kct))
+        eps_theta = max(eps_theta, eps_term + 2 * nprod * (-(-n_kct // nacct)) * 2.0 ** -23)
+    return 2.0 * (eps_proj + eps_theta)

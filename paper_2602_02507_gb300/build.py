@@ -15,8 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmultipole.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mp_api.cu", "mp_tables.cu", "mp_fp64.cu", "mp_radial.cu", "mp_split.cu", "mp_probe.cu", "mp_noalloc.cu",
-           "mp_gravity.cu", "mp_coarsen.cu"]
+SOURCES = ["mp_api.cu", "mp_tables.cu", "mp_fp64.cu", "mp_radial.cu", "mp_split.cu", "mp_theta_tc.cu", "mp_probe.cu",
+           "mp_noalloc.cu", "mp_gravity.cu", "mp_coarsen.cu"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
                      "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 

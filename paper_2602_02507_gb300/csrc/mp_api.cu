@@ -126,6 +126,25 @@ static mp_status make_map(CUtensorMap *map, const void *ptr, long long rows, int
     return MP_OK;
 }
 
+mp_status make_map_f32(CUtensorMap *map, const void *ptr, int rank, const unsigned long long *dims,
+                       const unsigned long long *strides_bytes, const unsigned *box, int swizzle128)
+{
+    auto fn = encode_fn();
+    if (!fn) return set_error(MP_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t d[3], st[2];
+    cuuint32_t b[3], es[3] = {1u, 1u, 1u};
+    for (int k = 0; k < rank; ++k) {
+        d[k] = dims[k];
+        b[k] = box[k];
+        if (k + 1 < rank) st[k] = strides_bytes[k];
+    }
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(ptr), d, st, b, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(MP_ERR_CUDA, "cuTensorMapEncodeTiled (float32) failed (%d)", (int)r);
+    return MP_OK;
+}
+
 // ---------------------------------------------------------------- helpers
 static bool finite_increasing(const double *e, int n)
 {
@@ -157,7 +176,8 @@ static void free_mesh_buffers(mp_mesh *m)
                     m->d_F64, m->d_G64,  m->d_F32,    m->d_C32,   m->d_Ith32, m->d_Itc32, m->d_Itc0, m->d_C0, m->d_colsum,
                     m->d_tabB, m->d_tabT, m->d_Aop, m->d_G0, m->phi_own, m->h_rho[0], m->h_rho[1],
                     m->h_phi[0], m->h_phi[1], m->d_err, m->d_gst, m->d_cwork, m->d_cweights, m->d_cgroups,
-                    m->d_cchunks, m->d_cscratch, m->d_ccount};
+                    m->d_cchunks, m->d_cscratch, m->d_ccount, m->d_tabTh, m->d_tabGs, m->d_Cb, m->d_th_off,
+                    m->d_gs_off, m->d_cb_off};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &pe : m->prof_pending) {
@@ -471,6 +491,34 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
             cudaMemsetAsync(m->d_Ith32, 0, (size_t)m->T * pl.ldF * sizeof(float), m->stream);
             cudaMemsetAsync(m->d_Itc32, 0, (size_t)m->T * pl.ldF * sizeof(float), m->stream);
         }
+        // orders m >= 1 of both theta stages on the tensor cores: pre-split tables, the
+        // coefficient terms (zero padding never written), the 3-D TMA map of F
+        std::vector<unsigned long long> th_off, gs_off, cb_off;
+        size_t th_bytes = 0, gs_bytes = 0, cb_bytes = 0;
+        if (plan_theta_tc(m, th_off, th_bytes, gs_off, gs_bytes, cb_off, cb_bytes)) {
+            ALLOC(m->d_tabTh, th_bytes);
+            ALLOC(m->d_tabGs, gs_bytes);
+            ALLOC(m->d_Cb, cb_bytes);
+            ALLOC(m->d_th_off, (size_t)(l_max + 1));
+            ALLOC(m->d_gs_off, (size_t)(l_max + 1));
+            ALLOC(m->d_cb_off, (size_t)(l_max + 1));
+            st = cuda_status(cudaMemsetAsync(m->d_Cb, 0, cb_bytes, m->stream), "clear coefficient terms");
+            if (st != MP_OK) return fail(st);
+            const size_t ob = (size_t)(l_max + 1) * sizeof(unsigned long long);
+            st = cuda_status(cudaMemcpy(m->d_th_off, th_off.data(), ob, cudaMemcpyHostToDevice), "table offsets");
+            if (st == MP_OK)
+                st = cuda_status(cudaMemcpy(m->d_gs_off, gs_off.data(), ob, cudaMemcpyHostToDevice), "table offsets");
+            if (st == MP_OK)
+                st = cuda_status(cudaMemcpy(m->d_cb_off, cb_off.data(), ob, cudaMemcpyHostToDevice), "table offsets");
+            if (st != MP_OK) return fail(st);
+            const unsigned long long dims[3] = {(unsigned long long)pl.ldF, (unsigned long long)m->P,
+                                                (unsigned long long)n_r};
+            const unsigned long long strides[2] = {(unsigned long long)pl.ldF * 4,
+                                                   (unsigned long long)m->P * pl.ldF * 4};
+            const unsigned box[3] = {32u, 1u, 64u};
+            st = make_map_f32(&m->tm_F, m->d_F32, 3, dims, strides, box, 1);
+            if (st != MP_OK) return fail(st);
+        }
     }
 #undef ALLOC
     {
@@ -489,6 +537,8 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
         if (st != MP_OK) return fail(st);
         if (m->eff_prec != MP_PREC_FP64) {
             st = cuda_status(launch_split_tables(m), "build split tables");
+            if (st != MP_OK) return fail(st);
+            st = cuda_status(launch_theta_tc_tables(m), "build tensor-core theta tables");
             if (st != MP_OK) return fail(st);
         }
         st = cuda_status(cudaStreamSynchronize(m->stream), "table build");
@@ -547,6 +597,7 @@ mp_status mp_mesh_get_info(const mp_mesh *m, mp_mesh_info *info)
     info->G = m->G;
     info->device_bytes = m->device_bytes;
     info->tuned_candidates = m->tuned_candidates;
+    info->theta_tensor_cores = m->eff_prec != MP_PREC_FP64 ? m->plan.use_theta_tc : 0;
     return MP_OK;
 }
 
@@ -658,6 +709,22 @@ mp_status mp_mesh_synchronize(mp_mesh *m)
         if (err & DEV_ERR_TIMEOUT) return set_error(MP_ERR_TIMEOUT, "a device-side pipeline wait ran out of time");
         if (err & DEV_ERR_NONFINITE) return set_error(MP_ERR_NONFINITE, "density holds NaN or infinity");
         return set_error(MP_ERR_CUDA, "device error word %d", err);
+    }
+    return MP_OK;
+}
+
+mp_status mp_set_theta_engine(mp_mesh *m, int engine)
+{
+    if (!m) return set_error(MP_ERR_INVALID_ARG, "mesh is NULL");
+    if (engine < 0 || engine > 2) return set_error(MP_ERR_INVALID_ARG, "engine must be 0, 1 or 2");
+    if (engine == 1 && !m->plan.theta_tc_ok)
+        return set_error(MP_ERR_UNSUPPORTED, "the tensor-core theta stages need the split path and l_max >= 1");
+    DeviceGuard dg(m->device);
+    MP_TRY(cudaStreamSynchronize(m->stream));
+    const int want = engine == 0 ? m->plan.theta_tc_default : (engine == 1 ? 1 : 0);
+    if (want != m->plan.use_theta_tc) {
+        m->plan.use_theta_tc = want;
+        drop_graph(m);
     }
     return MP_OK;
 }
@@ -907,19 +974,21 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
         std::string line;
         while (std::getline(f, line)) {
             std::istringstream is(line);
-            int a, b, c, d, e, ns_s, ns_b, sw, br;
-            if (is >> a >> b >> c >> d >> e >> ns_s >> ns_b >> sw >> br) {
+            int a, b, c, d, e, ns_s, ns_b, sw, br, tc;
+            if (is >> a >> b >> c >> d >> e >> ns_s >> ns_b >> sw >> br >> tc) {
                 std::ostringstream k;
                 k << a << ' ' << b << ' ' << c << ' ' << d << ' ' << e;
                 // a line that does not fit this plan's reserved memory (or an odd density
                 // ring, which the converter groups cannot share) is not used
                 const bool fits = ns_s >= 2 && !(ns_s & 1) && ns_s <= m->plan.ns_s_max && ns_b >= 1 &&
-                                  ns_b <= m->plan.ns_b_max && (sw == 64 || sw == 128 || sw == 256);
+                                  ns_b <= m->plan.ns_b_max && (sw == 64 || sw == 128 || sw == 256) &&
+                                  (tc == 0 || m->plan.theta_tc_ok);
                 if (k.str() == key && fits) {
                     m->plan.ns_s = ns_s;
                     m->plan.ns_b = ns_b;
                     m->plan.scan_threads = sw;
                     m->plan.proj_b_resident = br ? m->plan.proj_res_ok : !m->plan.proj_ring_ok;
+                    m->plan.use_theta_tc = tc;
                     m->tuned_candidates = 0;
                     drop_graph(m);
                     return MP_OK;
@@ -935,21 +1004,23 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     }
     const SplitPlan base = m->plan;
     struct Cand {
-        int ns_s, ns_b, sw, br;
+        int ns_s, ns_b, sw, br, tc;
     };
     std::vector<Cand> cands;
     const int sws[] = {64, 128, 256};
     if (m->eff_prec == MP_PREC_FP64) {
-        for (int sw : sws) cands.push_back({base.ns_s, base.ns_b, sw, 0});
+        for (int sw : sws) cands.push_back({base.ns_s, base.ns_b, sw, 0, 0});
     } else {
         // the synthesis table ring depth only matters when the table is not resident
         const int ns_b_lo = base.b_resident ? base.ns_b_max : 2;
-        // even density-ring depths only (the converter groups alternate over its slots)
-        for (int ns_s = 2; ns_s <= base.ns_s_max; ns_s += 2)
-            for (int ns_b = ns_b_lo; ns_b <= base.ns_b_max; ++ns_b)
-                for (int br = 0; br <= 1; ++br)
-                    if (br ? base.proj_res_ok : base.proj_ring_ok)
-                        for (int sw : sws) cands.push_back({ns_s, ns_b, sw, br});
+        // even density-ring depths only (the converter groups alternate over its slots); the
+        // theta stages on the tensor cores or on the CUDA cores
+        for (int tc = 0; tc <= base.theta_tc_ok; ++tc)
+            for (int ns_s = 2; ns_s <= base.ns_s_max; ns_s += 2)
+                for (int ns_b = ns_b_lo; ns_b <= base.ns_b_max; ++ns_b)
+                    for (int br = 0; br <= 1; ++br)
+                        if (br ? base.proj_res_ok : base.proj_ring_ok)
+                            for (int sw : sws) cands.push_back({ns_s, ns_b, sw, br, tc});
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -957,13 +1028,14 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     const int saved_prof = m->profiling;
     m->profiling = 0;
     float best = FLT_MAX;
-    Cand best_c = {base.ns_s, base.ns_b, base.scan_threads, base.proj_b_resident};
+    Cand best_c = {base.ns_s, base.ns_b, base.scan_threads, base.proj_b_resident, base.use_theta_tc};
     mp_status st = MP_OK;
     for (const Cand &c : cands) {
         m->plan.ns_s = c.ns_s;
         m->plan.ns_b = c.ns_b;
         m->plan.scan_threads = c.sw;
         m->plan.proj_b_resident = c.br;
+        m->plan.use_theta_tc = c.tc;
         st = run_solve(m, m->rho, phi);  // warm-up
         if (st != MP_OK) break;
         cudaEventRecord(e0, m->stream);
@@ -990,6 +1062,7 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     m->plan.ns_b = best_c.ns_b;
     m->plan.scan_threads = best_c.sw;
     m->plan.proj_b_resident = best_c.br;
+    m->plan.use_theta_tc = best_c.tc;
     m->tuned_candidates = (int)cands.size();
     drop_graph(m);
     if (st != MP_OK) {
@@ -998,7 +1071,8 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     }
     if (cache_path) {
         std::ofstream f(cache_path, std::ios::app);
-        f << key << ' ' << best_c.ns_s << ' ' << best_c.ns_b << ' ' << best_c.sw << ' ' << best_c.br << '\n';
+        f << key << ' ' << best_c.ns_s << ' ' << best_c.ns_b << ' ' << best_c.sw << ' ' << best_c.br << ' '
+          << best_c.tc << '\n';
     }
     return mp_mesh_synchronize(m);
 }

@@ -47,6 +47,21 @@ struct SplitPlan {
     int b_resident = 0;   // synthesis: whole table held in shared memory
     int stg_bufs = 2;     // synthesis: TMA store staging boxes per epilogue warp
     int scan_threads = 128;  // radial recurrences: threads (shell chunks) per moment column
+    // theta stages on the tensor cores (orders m >= 1; mp_theta_tc.cu): possible for this mesh
+    // (tables built), in use, and the choice the rule makes
+    int theta_tc_ok = 0, use_theta_tc = 0, theta_tc_default = 0;
+    int th_Nmax = 0, th_n_kc = 0, th_groups = 0, th_units = 0, th_nacc = 1, th_ns_s = 4, th_ns_o = 2, th_smem = 0;
+    int gs_NS = 8, gs_n_jb = 0, gs_n_sg = 0, gs_n_mg = 0, gs_units = 0, gs_ns_s = 4, gs_smem = 0;
+};
+
+// Where the radial recurrences write the solution coefficients C[i][l^2 + p] (m >= 1) as
+// the bf16 terms of the theta synthesis B operand: order m's block at cb + off[m], then
+// [shell group i / NS][K chunk (l - m) / 32][term][2 NS rows (shell, cos | sin) x 32]
+// canonical K-major (nullptr cb: not written).
+struct CbOut {
+    uint8_t *cb = nullptr;
+    const unsigned long long *off = nullptr;
+    int NS = 8, terms = 2, L = 0;
 };
 
 // Centred difference along one axis at one cell: (Phi[hi] - Phi[lo]) * w, w = 1 / (x_c[hi] - x_c[lo])
@@ -122,6 +137,11 @@ struct mp_mesh {
     double *d_cscratch = nullptr;  // per field of a launch: polar sums of the chunks
     int *d_ccount = nullptr;       // per field of a launch and many-row block: finished chunks
     double *d_cweights = nullptr;
+    // tensor-core theta stages: pre-split tables, their per-order byte offsets, the coefficient
+    // terms written by the radial recurrences, and the TMA map of F ([n_r][P][ldF] float32)
+    uint8_t *d_tabTh = nullptr, *d_tabGs = nullptr, *d_Cb = nullptr;
+    unsigned long long *d_th_off = nullptr, *d_gs_off = nullptr, *d_cb_off = nullptr;
+    CUtensorMap tm_F{};
     uint8_t *d_tabB = nullptr;    // projection B operand, bf16 x 3 terms, canonical layout
     uint8_t *d_tabT = nullptr;    // synthesis B operand, bf16 x 3 terms, canonical layout
     size_t tabB_chunk_bytes = 0, tabT_chunk_bytes = 0;
@@ -203,12 +223,25 @@ cudaError_t launch_fp64_synth(mp_mesh *m, double *phi);
 
 // ---- shared radial recurrences ----
 cudaError_t launch_scan(mp_mesh *m, int want_f32);
+// the CUDA-core theta contraction keeps its tables in shared memory (its fast form)
+bool theta_pipe_fits(const mp_mesh *m);
 
 // ---- split path ----
 cudaError_t launch_split_project(mp_mesh *m, const double *rho);
 cudaError_t launch_split_theta(mp_mesh *m);
 cudaError_t launch_split_synth(mp_mesh *m, double *phi);
 int split_smem_limits(mp_mesh *m);  // 0 when the plan fits, else an error
+
+// ---- tensor-core theta stages (orders m >= 1)
+bool plan_theta_tc(mp_mesh *m, std::vector<unsigned long long> &th_off, size_t &th_bytes,
+                   std::vector<unsigned long long> &gs_off, size_t &gs_bytes, std::vector<unsigned long long> &cb_off,
+                   size_t &cb_bytes);
+cudaError_t launch_theta_tc_tables(mp_mesh *m);
+cudaError_t launch_theta_tc(mp_mesh *m);   // theta contraction, m >= 1
+cudaError_t launch_gsynth_tc(mp_mesh *m);  // theta synthesis, m >= 1
+// tiled TMA map of a float32 array of up to 3 dimensions (innermost first)
+mp_status make_map_f32(CUtensorMap *map, const void *ptr, int rank, const unsigned long long *dims,
+                       const unsigned long long *strides_bytes, const unsigned *box, int swizzle128);
 
 // ---- gravitational source terms ----
 cudaError_t gravity_prepare(mp_mesh *m);  // stencils from the host edges (once per mesh)

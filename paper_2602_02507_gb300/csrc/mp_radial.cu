@@ -57,13 +57,32 @@ __device__ __forceinline__ void block_exclusive_scans(double xf, double xb, doub
     exb = ob + eb;
 }
 
+// C[i][l^2 + p] (m >= 1) as the bf16 terms of the tensor-core theta synthesis B operand
+// (layout: CbOut in mp_internal.h).
+__device__ __forceinline__ void write_cb(const CbOut &o, int i, int l, int p, float c32)
+{
+    const int m = pcol_m(p), a = (p + 1) & 1;
+    const int k = l - m, n_kcm = (o.L + 1 - m + 31) >> 5;
+    const int sg = i / o.NS, n = 2 * (i - sg * o.NS) + a;
+    const size_t c_term = (size_t)2 * o.NS * 64;
+    uint8_t *base = o.cb + o.off[m] + ((size_t)sg * n_kcm + (k >> 5)) * o.terms * c_term + (size_t)(n >> 3) * 512 +
+                    ((k & 31) >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(c32);
+    const float r1 = c32 - __bfloat162float(h0);
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+    *reinterpret_cast<__nv_bfloat16 *>(base) = h0;
+    *reinterpret_cast<__nv_bfloat16 *>(base + c_term) = h1;
+    if (o.terms == 3) *reinterpret_cast<__nv_bfloat16 *>(base + 2 * c_term) = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+}
+
 // One block per moment column q; thread t owns shells [t*chunk, (t+1)*chunk).
 template <int NT>
 __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const double *__restrict__ WR,
                                              const double *__restrict__ WI, const double *__restrict__ GR,
                                              const double *__restrict__ GI, double *__restrict__ MR,
                                              double *__restrict__ MI, double *__restrict__ C,
-                                             float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL)
+                                             float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL,
+                                             const CbOut cbo)
 {
     __shared__ double wt[2][NT / 32];
     // the next kernel's blocks may start (and copy their tables) while this one runs
@@ -108,8 +127,10 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
         double c = fma(GI[(size_t)l * n_r + i], mr_lo + mr_hi, GR[(size_t)l * n_r + i] * (mi + mi_hi));
         if (m > 0) c += c;
         C[(size_t)i * KL + q] = c;
-        if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(c);
+        const float c32 = f64_to_f32_alu(c);
+        if (C32) C32[(size_t)i * KL + q] = c32;
         if (C0 && p == 0) C0[(size_t)i * Lp1 + l] = f32_pair(c);
+        if (cbo.cb && p > 0) write_cb(cbo, i, l, p, c32);
     }
 }
 
@@ -120,7 +141,8 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
                                                  const double *__restrict__ WI, const double *__restrict__ GR,
                                                  const double *__restrict__ GI, double *__restrict__ MR,
                                                  double *__restrict__ MI, double *__restrict__ C,
-                                                 float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL)
+                                                 float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL,
+                                                 const CbOut cbo)
 {
     __shared__ double wt[2][NT / 32];
     // the next kernel's blocks may start (and copy their tables) while this one runs
@@ -173,8 +195,10 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
             double c = fma(g2[k], er[k] + er[k + 1], g1[k] * (ei[k] + ei[k + 1]));
             if (m > 0) c += c;
             C[(size_t)i * KL + q] = c;
-            if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(c);
+            const float c32 = f64_to_f32_alu(c);
+            if (C32) C32[(size_t)i * KL + q] = c32;
             if (C0 && p == 0) C0[(size_t)i * Lp1 + l] = f32_pair(c);
+            if (cbo.cb && p > 0) write_cb(cbo, i, l, p, c32);
         }
     }
     if (threadIdx.x == NT - 1) {
@@ -194,7 +218,8 @@ __global__ void __launch_bounds__(4 * NT) k_scan_q4(const double *__restrict__ A
                                                     const double *__restrict__ WI, const double *__restrict__ GR,
                                                     const double *__restrict__ GI, double *__restrict__ MR,
                                                     double *__restrict__ MI, double *__restrict__ C,
-                                                    float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL)
+                                                    float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL,
+                                                    const CbOut cbo)
 {
     constexpr int NW = 4 * NT / 32;
     __shared__ double wt[2][NW][4];
@@ -267,8 +292,10 @@ __global__ void __launch_bounds__(4 * NT) k_scan_q4(const double *__restrict__ A
             double cv = fma(__ldg(gi + i), er + er1, __ldg(gr + i) * (ei[k] + ei[k + 1]));
             if (m > 0) cv += cv;
             C[(size_t)i * KL + q] = cv;
-            if (C32) C32[(size_t)i * KL + q] = f64_to_f32_alu(cv);
+            const float c32 = f64_to_f32_alu(cv);
+            if (C32) C32[(size_t)i * KL + q] = c32;
             if (C0 && p == 0) C0[(size_t)i * Lp1 + l] = f32_pair(cv);
+            if (cbo.cb && p > 0) write_cb(cbo, i, l, p, c32);
             er = er1;
         }
     }
@@ -574,12 +601,26 @@ __global__ void __launch_bounds__(256) k32_theta_mgemm(const float *__restrict__
 
 }  // namespace
 
+// The coefficient terms of the tensor-core theta synthesis, when the split path uses it.
+static CbOut cb_out(const mp_mesh *m, int want_f32)
+{
+    CbOut o;
+    if (want_f32 && m->plan.use_theta_tc) {
+        o.cb = m->d_Cb;
+        o.off = m->d_cb_off;
+        o.NS = m->plan.gs_NS;
+        o.terms = m->plan.a_terms;
+        o.L = m->L;
+    }
+    return o;
+}
+
 template <int NT, int CH>
 static void scan_reg_launch(mp_mesh *m, int want_f32)
 {
     launch_pdl(k_scan_reg<NT, CH>, dim3(m->KL), dim3(NT), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
                m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, want_f32 ? m->d_C0 : nullptr, m->n_r,
-               m->KL);
+               m->KL, cb_out(m, want_f32));
 }
 
 // Shells per thread CH for NT threads per moment column; false when n_r > 16 NT.
@@ -618,6 +659,8 @@ static size_t theta_pipe_smem(const mp_mesh *m, int *n_items_out = nullptr, int 
     return tab_bytes + 2 * (size_t)P * ldF * 4 + (size_t)((n_items + 1) & ~1) * 4 + 3 * 8 + 16;
 }
 
+bool theta_pipe_fits(const mp_mesh *m) { return theta_pipe_smem(m) <= 200 * 1024; }
+
 // Four columns per block when there are at least four such blocks per SM; 128 chunk
 // threads per column (512 per block), CH shells each.  Not beside the persistent theta
 // contraction of the split path: its blocks leave room for the small one-column scan
@@ -630,7 +673,7 @@ static bool scan_q4_dispatch(mp_mesh *m, int want_f32)
     auto go = [&](auto kern) {
         launch_pdl(kern, dim3((m->KL + 3) / 4), dim3(512), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
                    m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, want_f32 ? m->d_C0 : nullptr, m->n_r,
-                   m->KL);
+                   m->KL, cb_out(m, want_f32));
     };
     if (ch <= 4)
         go(k_scan_q4<128, 4>);
@@ -657,21 +700,23 @@ cudaError_t launch_scan(mp_mesh *m, int want_f32)
         k_scan<kScanThreads><<<m->KL, kScanThreads, 0, m->stream>>>(m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
                                                                     m->d_MR, m->d_MI, m->d_C,
                                                                     want_f32 ? m->d_C32 : nullptr,
-                                                                    want_f32 ? m->d_C0 : nullptr, m->n_r, m->KL);
+                                                                    want_f32 ? m->d_C0 : nullptr, m->n_r, m->KL,
+                                                                    cb_out(m, want_f32));
     prof_end(m, "radial_scan", ev);
     return cudaGetLastError();
 }
 
 
-cudaError_t launch_split_theta(mp_mesh *m)
+// The theta contraction of the orders 0 .. orders_hi on CUDA cores (all of them when the
+// tensor-core kernel does not apply).
+static cudaError_t theta_cuda_cores(mp_mesh *m, int orders_hi)
 {
     constexpr double kFourPi = 12.566370614359172954;
     const int ldF = m->plan.ldF, L = m->L, P = m->P;
     const uint32_t tab_bytes = (uint32_t)((size_t)m->T * ldF * 4);
     int n_items = 0, jsh = 0;
     const size_t smem = theta_pipe_smem(m, &n_items, &jsh);
-    cudaEvent_t ev;
-    prof_begin(m, "split_theta_contract", &ev);
+    if (orders_hi == 0) n_items = (L + 2) / 2;  // the items of m = 0 come first
     if (smem <= 200 * 1024) {
         static bool attr_set = false;
         if (!attr_set) {
@@ -683,12 +728,26 @@ cudaError_t launch_split_theta(mp_mesh *m)
         launch_pdl(k32_theta_pipe, dim3(grid), dim3(threads), smem, m->stream, m->d_F32, m->d_Ith32, m->d_A, m->d_err,
                    m->n_r, m->n_t, L, m->KL, P, ldF, n_items, jsh, tab_bytes, kFourPi * m->G);
     } else {
-        const dim3 grid((m->n_r + kMgShells - 1) / kMgShells, L + 1);
+        const dim3 grid((m->n_r + kMgShells - 1) / kMgShells, orders_hi + 1);
         launch_pdl(k32_theta_mgemm, grid, dim3(256), 0, m->stream, m->d_F32, m->d_Ith32, m->d_A, m->n_r, m->n_t, L,
                    m->KL, P, ldF, kFourPi * m->G);
     }
-    prof_end(m, "split_theta_contract", ev);
     return cudaGetLastError();
+}
+
+cudaError_t launch_split_theta(mp_mesh *m)
+{
+    cudaEvent_t ev;
+    if (m->plan.use_theta_tc) {
+        prof_begin(m, "split_theta_contract_tc", &ev);
+        cudaError_t e = launch_theta_tc(m);
+        prof_end(m, "split_theta_contract_tc", ev);
+        return e;
+    }
+    prof_begin(m, "split_theta_contract", &ev);
+    cudaError_t e = theta_cuda_cores(m, m->L);
+    prof_end(m, "split_theta_contract", ev);
+    return e;
 }
 
 }  // namespace mp

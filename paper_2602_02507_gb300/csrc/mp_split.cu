@@ -39,14 +39,6 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 __constant__ int c_prod_a[6] = {0, 0, 1, 0, 1, 2};
 __constant__ int c_prod_b[6] = {0, 1, 0, 2, 1, 0};
 
-__device__ __forceinline__ uint32_t tmem_ncols_for(int cols)
-{
-    uint32_t n = 32;
-    while (n < (uint32_t)cols) n <<= 1;
-    return n;
-}
-
-__device__ __forceinline__ bool warp_all(bool v) { return __all_sync(kFull, v); }
 
 // ----------------------------------------------------------------------------
 // (a1) phi projection
@@ -58,40 +50,6 @@ constexpr int S_BYTES = 2 * BOX_BYTES;       // 32 KB
 constexpr int A_TERM_BYTES = kBM * BK * 2;   // [128 x 32] bf16, 8 KB
 constexpr int SBO = (BK / 8) * 128;          // 8-row group stride of A and B chunks
 }  // namespace proj
-
-// Position in a ring of mbarrier-guarded stages: index and phase advance together.
-struct Ring {
-    int idx = 0;
-    uint32_t phase = 0;
-    __device__ __forceinline__ void next(int n)
-    {
-        if (++idx == n) {
-            idx = 0;
-            phase ^= 1u;
-        }
-    }
-    __device__ __forceinline__ void prev(int n)
-    {
-        if (idx == 0) {
-            idx = n;
-            phase ^= 1u;
-        }
-        --idx;
-    }
-};
-
-// After an abort: waits (bounded by the full budget) for the last min(n, issued) copies
-// issued into the n-slot ring whose next free position is r, so that none of them is still
-// writing into this block's shared memory when the block exits.
-__device__ __forceinline__ void drain_ring(uint64_t *full, Ring r, int n, int issued)
-{
-    for (int k = 0; k < n && k < issued; ++k) {
-        r.prev(n);
-        const long long t0 = clock64();
-        while (!mbar_try_wait(smem_u32(&full[r.idx]), r.phase) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
-        }
-    }
-}
 
 // Chunk order of a tile: a rotation by a tile-dependent offset, so that the SMs
 // streaming different tiles address different parts of their rows at any moment
@@ -463,28 +421,6 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
 // pass's coefficients are read into registers during the output pass.
 constexpr int kGsS = 2;   // shells per pass
 constexpr int kGsPre = 4; // coefficient registers per thread (kGsS * KL <= kGsPre * threads)
-
-// The m = 0 column is the bulk of Phi and its Legendre sum can cancel: it is formed in
-// double-float arithmetic on the float32 pipe from (hi, lo) pairs of the table T[l] and
-// the coefficients c[l] -- products split exactly by fmaf, the running sum kept as a
-// TwoSum pair -- and leaves as a (hi, lo) pair (relative error near 2^-44).
-__device__ __forceinline__ float2 g0_double_float(const float2 *T, int t_stride, const float2 *c, int L)
-{
-    float s = 0.0f, e = 0.0f;
-    for (int l = 0; l <= L; ++l) {
-        const float2 t = T[(size_t)l * t_stride], k = c[l];
-        const float p = __fmul_rn(t.x, k.x);
-        const float pe = fmaf(t.x, k.x, -p);            // exact error of the leading product
-        const float cross = fmaf(t.x, k.y, __fmul_rn(t.y, k.x));
-        const float s2 = __fadd_rn(s, p);                 // TwoSum of the running sum and p
-        const float bv = __fsub_rn(s2, s);
-        const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bv)), __fsub_rn(p, bv));
-        s = s2;
-        e = __fadd_rn(e, __fadd_rn(se, __fadd_rn(pe, cross)));
-    }
-    const float hi = __fadd_rn(s, e);
-    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
-}
 
 template <int A_TERMS>
 __global__ void __launch_bounds__(1024, 1) k_gsynth_pipe(const float *__restrict__ C32, const float *__restrict__ Itc,
@@ -1293,12 +1229,20 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho)
     return cudaGetLastError();
 }
 
+static cudaError_t launch_phi_synth(mp_mesh *m);
+
 cudaError_t launch_split_synth(mp_mesh *m, double *phi)
 {
     (void)phi;
-    const SplitPlan &pl = m->plan;
-    const int n_tiles = (int)((m->R + kBM - 1) / kBM);
     cudaEvent_t ev;
+    if (m->plan.use_theta_tc) {
+        prof_begin(m, "split_theta_synth_tc", &ev);
+        cudaError_t e = launch_gsynth_tc(m);
+        prof_end(m, "split_theta_synth_tc", ev);
+        if (e != cudaSuccess) return e;
+        return launch_phi_synth(m);
+    }
+    const SplitPlan &pl = m->plan;
     prof_begin(m, "split_theta_synth", &ev);
     const uint32_t tab_bytes = (uint32_t)((size_t)m->T * pl.ldF * 4);
     const int U = (m->L + 1) / 2, NJ = ((m->n_t + 3) / 4 + 31) / 32;
@@ -1336,6 +1280,14 @@ cudaError_t launch_split_synth(mp_mesh *m, double *phi)
                        m->n_r, m->n_t, m->L, m->KL, pl.Kpad, pl.ldF);
     }
     prof_end(m, "split_theta_synth", ev);
+    return launch_phi_synth(m);
+}
+
+static cudaError_t launch_phi_synth(mp_mesh *m)
+{
+    const SplitPlan &pl = m->plan;
+    const int n_tiles = (int)((m->R + kBM - 1) / kBM);
+    cudaEvent_t ev;
     SynthParams prm;
     prm.Aop = m->d_Aop;
     prm.G0 = m->d_G0;

@@ -86,6 +86,50 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Position in a ring of mbarrier-guarded stages: index and phase advance together.
+struct Ring {
+    int idx = 0;
+    uint32_t phase = 0;
+    __device__ __forceinline__ void next(int n)
+    {
+        if (++idx == n) {
+            idx = 0;
+            phase ^= 1u;
+        }
+    }
+    __device__ __forceinline__ void prev(int n)
+    {
+        if (idx == 0) {
+            idx = n;
+            phase ^= 1u;
+        }
+        --idx;
+    }
+};
+
+// After an abort: waits (bounded by the full budget) for the last min(n, issued) copies
+// issued into the n-slot ring whose next free position is r, so that none of them is still
+// writing into this block's shared memory when the block exits.
+__device__ __forceinline__ void drain_ring(uint64_t *full, Ring r, int n, int issued)
+{
+    for (int k = 0; k < n && k < issued; ++k) {
+        r.prev(n);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(smem_u32(&full[r.idx]), r.phase) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
+        }
+    }
+}
+
+// Tensor-memory allocation size: a power of two of at least 32 columns.
+__device__ __forceinline__ uint32_t tmem_ncols_for(int cols)
+{
+    uint32_t n = 32;
+    while (n < (uint32_t)cols) n <<= 1;
+    return n;
+}
+
+__device__ __forceinline__ bool warp_all(bool v) { return __all_sync(0xFFFFFFFFu, v); }
+
 // ---------------------------------------------------------------- programmatic dependent launch
 // Blocks until the grids this one depends on (the previous kernel on the
 // stream, when launched with programmatic stream serialization) have completed
@@ -110,6 +154,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *map, uint3
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
         "l"(map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void *map, uint32_t bar, int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(x), "r"(y), "r"(z)
         : "memory");
 }
 
@@ -382,5 +435,27 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float x, float y)
 
 __device__ __forceinline__ float bf16lo_to_f32(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16hi_to_f32(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// The m = 0 column is the bulk of Phi and its Legendre sum can cancel: it is formed in
+// double-float arithmetic on the float32 pipe from (hi, lo) pairs of the table T[l] and
+// the coefficients c[l] -- products split exactly by fmaf, the running sum kept as a
+// TwoSum pair -- and leaves as a (hi, lo) pair (relative error near 2^-44).
+__device__ __forceinline__ float2 g0_double_float(const float2 *T, int t_stride, const float2 *c, int L)
+{
+    float s = 0.0f, e = 0.0f;
+    for (int l = 0; l <= L; ++l) {
+        const float2 t = T[(size_t)l * t_stride], k = c[l];
+        const float p = __fmul_rn(t.x, k.x);
+        const float pe = fmaf(t.x, k.x, -p);            // exact error of the leading product
+        const float cross = fmaf(t.x, k.y, __fmul_rn(t.y, k.x));
+        const float s2 = __fadd_rn(s, p);                 // TwoSum of the running sum and p
+        const float bv = __fsub_rn(s2, s);
+        const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bv)), __fsub_rn(p, bv));
+        s = s2;
+        e = __fadd_rn(e, __fadd_rn(se, __fadd_rn(pe, cross)));
+    }
+    const float hi = __fadd_rn(s, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
 
 }  // namespace mp

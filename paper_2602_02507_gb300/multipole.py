@@ -36,7 +36,8 @@ class MeshInfo(ctypes.Structure):
     _fields_ = [("n_r", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
                 ("l_max", ctypes.c_int), ("n_moments", ctypes.c_int), ("precision", ctypes.c_int),
                 ("effective_precision", ctypes.c_int), ("r_ref", ctypes.c_double), ("G", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t), ("tuned_candidates", ctypes.c_int)]
+                ("device_bytes", ctypes.c_size_t), ("tuned_candidates", ctypes.c_int),
+                ("theta_tensor_cores", ctypes.c_int)]
 
 
 def load_library(path: str = LIB_PATH):
@@ -63,6 +64,7 @@ def load_library(path: str = LIB_PATH):
         "mp_solve_host_async": [vp, vp, vp],
         "mp_mesh_synchronize": [vp],
         "mp_set_wait_budget": [vp, ctypes.c_longlong],
+        "mp_set_theta_engine": [vp, i],
         "mp_profile_enable": [vp, i],
         "mp_profile_read": [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i), dp, i, ctypes.POINTER(i)],
         "mp_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(vp)],
@@ -244,6 +246,12 @@ class Mesh:
 
     def synchronize(self):
         _check(self._lib.mp_mesh_synchronize(self._h), "mp_mesh_synchronize")
+
+    def set_theta_engine(self, engine: str):
+        """Engine of the theta stages on the split path: "auto", "tensor" (tcgen05 for the
+        orders m >= 1) or "cuda" (every order on CUDA cores)."""
+        code = {"auto": 0, "tensor": 1, "cuda": 2}[engine]
+        _check(self._lib.mp_set_theta_engine(self._h, code), "mp_set_theta_engine")
 
     def set_wait_budget(self, cycles: int):
         """Budget of the device-side pipeline waits in SM clock cycles (0: the default)."""

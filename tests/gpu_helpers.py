@@ -2,7 +2,9 @@
 import numpy as np
 
 
-def gpu_solve(w, precision, want_moments=True):
+def gpu_solve(w, precision, want_moments=True, engine=None):
+    """One solve through the C ABI; engine selects the theta stages of the split path
+    ("tensor" or "cuda"; None keeps the mesh's default)."""
     import torch
 
     from paper_2602_02507_gb300 import multipole as mpl
@@ -11,6 +13,8 @@ def gpu_solve(w, precision, want_moments=True):
     rho = torch.from_numpy(np.ascontiguousarray(w.rho)).cuda()
     phi = torch.empty_like(rho)
     with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=precision) as mesh:
+        if engine is not None:
+            mesh.set_theta_engine(engine)
         mesh.set_density(rho)
         mesh.set_phi_output(phi)
         mesh.solve()

@@ -57,4 +57,4 @@ def test_split_bar_grows_with_the_accumulation_chain():
     large = W.presn(n_r=4, n_theta=8, n_phi=1024, L=64, materialize=False).mesh
     assert split_moment_bar(small, "bf16x3") < split_moment_bar(large, "bf16x3")
     assert split_moment_bar(small, "bf16x6") < split_moment_bar(small, "bf16x3")
-    assert split_moment_bar(large, "bf16x3") < 1e-4
+    assert split_moment_bar(large, "bf16x3") < 2e-4

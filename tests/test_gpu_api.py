@@ -34,8 +34,9 @@ def test_nonfinite_density_is_reported(prec):
         mesh.synchronize()  # the error word was cleared
 
 
+@pytest.mark.parametrize("engine", ["tensor", "cuda"])
 @pytest.mark.parametrize("shape,L", [((8, 16, 32), 4), ((64, 32, 64), 8)])
-def test_expired_device_wait_reports_timeout_and_the_mesh_recovers(shape, L):
+def test_expired_device_wait_reports_timeout_and_the_mesh_recovers(shape, L, engine):
     """Failure detection without a fault: a wait budget of one clock cycle makes the
     bounded pipeline waits of the split kernels run out.  Every block then raises its
     abort flag, lets the copies and MMAs it issued finish, frees its tensor memory and
@@ -50,6 +51,7 @@ def test_expired_device_wait_reports_timeout_and_the_mesh_recovers(shape, L):
     phi = torch.empty_like(rho)
     with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3") as mesh:
         assert mesh.info()["effective_precision"] == 1
+        mesh.set_theta_engine(engine)
         mesh.set_density(rho)
         mesh.set_phi_output(phi)
         mesh.solve()
@@ -188,20 +190,23 @@ def test_batch_equals_individual_solves():
         mesh.close()
 
 
-def test_profile_names_every_kernel():
+@pytest.mark.parametrize("engine", ["tensor", "cuda"])
+def test_profile_names_every_kernel(engine):
     import torch
     from paper_2602_02507_gb300 import multipole as mpl
     w = W.presn(n_r=16, n_theta=32, n_phi=64, L=8)
     m = w.mesh
     rho = torch.from_numpy(w.rho).cuda()
     with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3") as mesh:
+        mesh.set_theta_engine(engine)
         mesh.set_density(rho)
         mesh.profile(True)
         for _ in range(3):
             mesh.solve()
         prof = mesh.profile_read()
-    assert set(prof) == {"split_phi_project_tc", "split_theta_contract", "radial_scan", "split_theta_synth",
-                         "split_synth_tc"}
+    theta = {"tensor": ("split_theta_contract_tc", "split_theta_synth_tc"),
+             "cuda": ("split_theta_contract", "split_theta_synth")}[engine]
+    assert set(prof) == {"split_phi_project_tc", "radial_scan", "split_synth_tc", *theta}
     assert all(v["launches"] == 3 and v["total_ms"] > 0 for v in prof.values())
 
 
@@ -219,6 +224,7 @@ def test_autotune_keeps_results(tmp_path):
         mesh.set_phi_output(phi)
         mesh.autotune(cache)
         assert mesh.info()["tuned_candidates"] > 1  # configurations were actually timed
+        engine = mesh.info()["theta_tensor_cores"]
         mesh.solve()
         mesh.synchronize()
         assert phi_rel_err(phi.cpu().numpy(), ref) <= 1e-6
@@ -227,3 +233,4 @@ def test_autotune_keeps_results(tmp_path):
         mesh2.set_density(rho)
         mesh2.autotune(cache)  # served from the cache
         assert mesh2.info()["tuned_candidates"] == 0
+        assert mesh2.info()["theta_tensor_cores"] == engine

@@ -29,8 +29,9 @@ def _built():
     g.build()
 
 
-def _solve(w, prec, rho_dev=None, shells=None):
-    """Phi (whole mesh, or the listed shells), the angular and edge moments of one GPU solve."""
+def _solve(w, prec, rho_dev=None, shells=None, engine=None):
+    """Phi (whole mesh, or the listed shells), the angular and edge moments of one GPU solve
+    (engine: theta stages of the split path, "tensor" or "cuda"; None: the default)."""
     import torch
     from paper_2602_02507_gb300 import multipole as mpl
     m = w.mesh
@@ -41,6 +42,8 @@ def _solve(w, prec, rho_dev=None, shells=None):
     MR = torch.empty((n_r + 1) * K, dtype=torch.float64, device="cuda")
     MI = torch.empty((n_r + 1) * K, dtype=torch.float64, device="cuda")
     with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=prec) as mesh:
+        if engine is not None:
+            mesh.set_theta_engine(engine)
         mesh.set_density(rho)
         mesh.set_phi_output(phi)
         mesh.solve()
@@ -74,13 +77,15 @@ def test_lognormal_full_size_1024x256x512_L32():
     ref = O.solve(tab, w.rho, m.G)
     ref["tables"] = tab
     S = term_scales(w.rho, tab, m.G)
-    for prec, tol in (("fp64", 1e-12), ("bf16x3", 1e-6), ("bf16x6", 1e-6)):
-        phi, mom, eff = _solve(w, prec)
+    for prec, tol, engine in (("fp64", 1e-12, None), ("bf16x3", 1e-6, "tensor"), ("bf16x6", 1e-6, "tensor"),
+                              ("bf16x3", 1e-6, "cuda")):
+        phi, mom, eff = _solve(w, prec, engine=engine)
         assert eff == {"fp64": 0, "bf16x3": 1, "bf16x6": 2}[prec]
         err = phi_rel_err(phi, ref["phi"])
-        print(f"lognormal {prec}: phi {err:.3e}, per-l A vs degree max {max(per_l_errors(mom['A'], ref['A'], m.L)):.3e}")
-        assert err <= tol, (prec, err)
-        _check_moments("lognormal", w, prec, mom, ref, S, m.L)
+        print(f"lognormal {prec} {engine}: phi {err:.3e}, per-l A vs degree max "
+              f"{max(per_l_errors(mom['A'], ref['A'], m.L)):.3e}")
+        assert err <= tol, (prec, engine, err)
+        _check_moments(f"lognormal {engine}", w, prec, mom, ref, S, m.L)
 
 
 LARGE_SHELLS = sorted(set([0, 1, 2046, 2047] + list(range(0, 2048, 32))))
@@ -101,15 +106,15 @@ def test_large_full_size_2048x512x1024_L64_sampled_shells():
     import torch
     rho = torch.from_numpy(w.rho).cuda()
     del w
-    for prec in ("fp64", "bf16x3"):
-        phi, mom, _ = _solve(W.large(), prec, rho_dev=rho, shells=shells)
+    for prec, engine in (("fp64", None), ("bf16x3", "tensor"), ("bf16x3", "cuda")):
+        phi, mom, _ = _solve(W.large(), prec, rho_dev=rho, shells=shells, engine=engine)
         pointwise = phi_rel_err(phi, ref_phi)
         maxnorm = float(np.abs(phi - ref_phi).max() / np.abs(ref_phi).max())
         A = mom["A"]
         mono = float(np.max(np.abs(A[:, 0] - ref["A"][:, 0]) / np.abs(ref["A"][:, 0])))
-        print(f"large {prec}: phi pointwise {pointwise:.3e}, max-norm {maxnorm:.3e}, A_00 {mono:.3e}")
-        assert pointwise <= (1e-12 if prec == "fp64" else 1e-6), (prec, pointwise, maxnorm, mono)
-        _check_moments("large", W.large(), prec, mom, ref, S, m.L)
+        print(f"large {prec} {engine}: phi pointwise {pointwise:.3e}, max-norm {maxnorm:.3e}, A_00 {mono:.3e}")
+        assert pointwise <= (1e-12 if prec == "fp64" else 1e-6), (prec, engine, pointwise, maxnorm, mono)
+        _check_moments(f"large {engine}", W.large(), prec, mom, ref, S, m.L)
         torch.cuda.empty_cache()
 
 

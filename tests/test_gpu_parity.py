@@ -92,12 +92,17 @@ SPLIT_CASES = {
 }
 
 
+@pytest.mark.parametrize("engine", ["tensor", "cuda"])
 @pytest.mark.parametrize("name,prec", [(n, p) for n, (_, ps) in SPLIT_CASES.items() for p in ps])
-def test_split_path_matches_oracle(name, prec):
+def test_split_path_matches_oracle(name, prec, engine):
+    """Both engines of the theta stages: tcgen05 GEMMs per order (m >= 1) and CUDA cores."""
     w = SPLIT_CASES[name][0]()
+    if engine == "tensor" and w.mesh.L == 0:
+        pytest.skip("l_max = 0 has no orders m >= 1")
     ref = oracle_solve(w)
-    got = gpu_solve(w, prec)
+    got = gpu_solve(w, prec, engine=engine)
     assert got["info"]["effective_precision"] == {"bf16x3": 1, "bf16x6": 2}[prec]
+    assert got["info"]["theta_tensor_cores"] == (1 if engine == "tensor" else 0)
     err = phi_rel_err(got["phi"], ref["phi"])
     assert err <= 1e-6, err
     # every exported moment, per degree: the angular moments of step (a) and the edge
@@ -108,7 +113,7 @@ def test_split_path_matches_oracle(name, prec):
     bar = split_moment_bar(w.mesh, prec)
     eA = moment_term_errors(got["A"], ref["A"], S, L)
     eM = edge_term_errors(got, ref, S)
-    print(f"{name} {prec}: phi {err:.2e}; per-l A/S max {max(eA):.2e}, M^R {max(eM['MR']):.2e}, "
+    print(f"{name} {prec} {engine}: phi {err:.2e}; per-l A/S max {max(eA):.2e}, M^R {max(eM['MR']):.2e}, "
           f"M^I {max(eM['MI']):.2e} (bar {bar:.2e}); per-l A vs degree max {max(per_l_errors(got['A'], ref['A'], L)):.2e}")
     assert max(eA) <= bar, eA
     assert max(eM["MR"]) <= bar, eM["MR"]
@@ -118,12 +123,27 @@ def test_split_path_matches_oracle(name, prec):
 
 
 def test_presn_full_size_split_and_fp64():
-    """512 x 128 x 256 cells, L = 16: every cell against the oracle, both paths."""
+    """512 x 128 x 256 cells, L = 16: every cell against the oracle, both paths (the split
+    path with both theta engines)."""
     w = W.presn()
     ref = oracle_solve(w)
-    for prec, tol in (("bf16x3", 1e-6), ("fp64", 1e-12)):
-        got = gpu_solve(w, prec, want_moments=False)
-        assert phi_rel_err(got["phi"], ref["phi"]) <= tol, prec
+    for prec, tol, engine in (("bf16x3", 1e-6, "tensor"), ("bf16x3", 1e-6, "cuda"), ("fp64", 1e-12, None)):
+        got = gpu_solve(w, prec, want_moments=False, engine=engine)
+        assert phi_rel_err(got["phi"], ref["phi"]) <= tol, (prec, engine)
+
+
+def test_theta_engine_requests_that_cannot_be_served():
+    from paper_2602_02507_gb300 import multipole as mpl
+    for prec, L in (("fp64", 4), ("bf16x3", 0)):
+        w = W.presn(n_r=8, n_theta=16, n_phi=32, L=L, materialize=False)
+        m = w.mesh
+        with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision=prec) as mesh:
+            with pytest.raises(mpl.MultipoleError) as ei:
+                mesh.set_theta_engine("tensor")
+            assert ei.value.name == "MP_ERR_UNSUPPORTED"
+            mesh.set_theta_engine("cuda")
+            mesh.set_theta_engine("auto")
+            assert mesh.info()["theta_tensor_cores"] == 0
 
 
 def test_split_falls_back_to_fp64_for_odd_nphi():
