@@ -121,6 +121,42 @@ MP_API mp_status mp_mesh_create(const double *r_edges, int n_r, const double *th
                          const double *phi_edges, int n_phi, int l_max, double G, mp_precision prec,
                          void *cuda_stream, mp_mesh **out);
 
+/*
+ * Radial-shell domain decomposition (Sec. 2.1: the mesh is divided among processes
+ * into radial shells that each cover the full solid angle; Sec. 2.2: the moment sums
+ * are then combined across processes).  A slab holds shells [i0, i1) of a mesh whose
+ * n_r + 1 radial edges are r_edges; its radial kernels use the whole mesh's reference
+ * radius, so that the radial sums of different slabs add.  The radial recurrences of
+ * the whole mesh differ from a slab's own only by two constants per moment: the sum of
+ * W^R A over the slabs below it (added to every M^R edge) and the sum of W^I A over the
+ * slabs above it (added to every M^I edge).  A solve over P slabs is therefore
+ *   1. on every slab: mp_slab_moments -> its totals T[2][K_L] (device):
+ *      T[0][q] = sum over its shells of W^R_l A_q, T[1][q] = sum of W^I_l A_q;
+ *   2. one exclusive prefix over the slabs in radial order (2 K_L doubles each):
+ *      outer[0][q] = sum of T[0][q] over the slabs below, outer[1][q] = sum of T[1][q]
+ *      over the slabs above (paper_2602_02507_gb300.sharding does it with
+ *      torch.distributed, one slab per rank);
+ *   3. on every slab: mp_slab_potential(outer) -> its edge moments, coefficients
+ *      and Phi, equal to the whole mesh's on its shells up to rounding.
+ * Arguments as mp_mesh_create, plus 0 <= i0 < i1 <= n_r.  The slab's density and
+ * potential cover only its shells ([i1 - i0][n_theta][n_phi]); mp_solve on a slab
+ * solves it alone (no other slabs).  Errors as mp_mesh_create.
+ */
+MP_API mp_status mp_mesh_create_slab(const double *r_edges, int n_r, int i0, int i1, const double *theta_edges,
+                                     int n_theta, const double *phi_edges, int n_phi, int l_max, double G,
+                                     mp_precision prec, void *cuda_stream, mp_mesh **out);
+
+/* Step 1 above: angular moments of the bound density and this slab's radial totals
+ * (totals_dev: device [2][K_L], written on the mesh's stream).  Any mesh may call it.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_NOT_READY (no density bound). */
+MP_API mp_status mp_slab_moments(mp_mesh *mesh, double *totals_dev);
+
+/* Step 3 above: outer_dev (device [2][K_L]) holds the sums of the other slabs; writes
+ * the potential into the bound output and keeps the edge moments for mp_get_moments.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_NOT_READY (mp_slab_moments has not run since the
+ * last call). */
+MP_API mp_status mp_slab_potential(mp_mesh *mesh, const double *outer_dev);
+
 /* Release the mesh and every device buffer it owns (waits for its stream). */
 MP_API mp_status mp_mesh_destroy(mp_mesh *mesh);
 

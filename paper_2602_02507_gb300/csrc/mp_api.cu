@@ -177,7 +177,7 @@ static void free_mesh_buffers(mp_mesh *m)
                     m->d_tabB, m->d_tabT, m->d_Aop, m->d_G0, m->phi_own, m->h_rho[0], m->h_rho[1],
                     m->h_phi[0], m->h_phi[1], m->d_err, m->d_gst, m->d_cwork, m->d_cweights, m->d_cgroups,
                     m->d_cchunks, m->d_cscratch, m->d_ccount, m->d_tabTh, m->d_tabGs, m->d_Cb, m->d_th_off,
-                    m->d_gs_off, m->d_cb_off};
+                    m->d_gs_off, m->d_cb_off, m->d_slab_off};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &pe : m->prof_pending) {
@@ -217,29 +217,49 @@ static mp_status ensure_phi_own(mp_mesh *m)
     return dalloc(m, &m->phi_own, (size_t)m->N);
 }
 
-static mp_status run_solve(mp_mesh *m, const double *rho, double *phi)
+// Step (a): the angular moments of rho.
+static mp_status run_moments(mp_mesh *m, const double *rho)
 {
     if (m->eff_prec == MP_PREC_FP64) {
         MP_TRY(launch_fp64_project(m, rho));
         MP_TRY(launch_fp64_theta(m));
-        MP_TRY(launch_scan(m, 0));
-        MP_TRY(launch_fp64_synth(m, phi));
     } else {
         if (m->tm_rho_ptr != rho) {
             mp_status st = make_map(&m->tm_rho, rho, m->R, m->n_p, 128);
             if (st != MP_OK) return st;
             m->tm_rho_ptr = rho;
         }
+        MP_TRY(launch_split_project(m, rho));
+        MP_TRY(launch_split_theta(m));
+    }
+    return MP_OK;
+}
+
+// Steps (b)-(d): the radial recurrences (from the other slabs' sums when use_slab_off is
+// set) and the potential.
+static mp_status run_potential(mp_mesh *m, double *phi)
+{
+    if (m->eff_prec == MP_PREC_FP64) {
+        MP_TRY(launch_scan(m, 0));
+        MP_TRY(launch_fp64_synth(m, phi));
+    } else {
         if (m->tm_phi_ptr != phi) {
             mp_status st = make_map(&m->tm_phi, phi, m->R, m->n_p, 32);
             if (st != MP_OK) return st;
             m->tm_phi_ptr = phi;
         }
-        MP_TRY(launch_split_project(m, rho));
-        MP_TRY(launch_split_theta(m));
         MP_TRY(launch_scan(m, 1));
         MP_TRY(launch_split_synth(m, phi));
     }
+    return MP_OK;
+}
+
+static mp_status run_solve(mp_mesh *m, const double *rho, double *phi)
+{
+    mp_status st = run_moments(m, rho);
+    if (st != MP_OK) return st;
+    st = run_potential(m, phi);
+    if (st != MP_OK) return st;
     m->solved = 1;
     return MP_OK;
 }
@@ -369,9 +389,13 @@ mp_status mp_last_error_detail(char *buf, int len)
     return MP_OK;
 }
 
-mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edges, int n_theta,
-                         const double *phi_edges, int n_phi, int l_max, double G, mp_precision prec, void *cuda_stream,
-                         mp_mesh **out)
+}  // extern "C"
+
+// Mesh creation; r_ref_given > 0 fixes the reference radius of the radial kernels (a slab
+// of a larger mesh takes the whole mesh's), otherwise sqrt(r_min+ r_max) of these edges.
+static mp_status create_mesh(const double *r_edges, int n_r, const double *theta_edges, int n_theta,
+                             const double *phi_edges, int n_phi, int l_max, double G, mp_precision prec,
+                             void *cuda_stream, double r_ref_given, mp_mesh **out)
 {
     g_detail[0] = 0;
     if (!out) return set_error(MP_ERR_INVALID_ARG, "out is NULL");
@@ -395,7 +419,7 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
     // reference radius and float64 range of the scaled radial kernels
     const double rmin = r_edges[0] > 0.0 ? r_edges[0] : r_edges[1];
     const double rmax = r_edges[n_r];
-    const double r_ref = std::sqrt(rmin * rmax);
+    const double r_ref = r_ref_given > 0.0 ? r_ref_given : std::sqrt(rmin * rmax);
     {
         const double lx_hi = std::log10(rmax / r_ref), lx_lo = std::log10(rmin / r_ref), lr = std::log10(r_ref);
         const double e_reg = 3.0 * lr + (l_max + 3.0) * lx_hi;
@@ -460,7 +484,8 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
     ALLOC(m->d_MR, (size_t)(n_r + 1) * m->KL);
     ALLOC(m->d_MI, (size_t)(n_r + 1) * m->KL);
     ALLOC(m->d_C, (size_t)n_r * m->KL);
-    ALLOC(m->d_err, 4);  // [0] error word, [2..3] budget of the pipeline waits (int64, 0: default)
+    ALLOC(m->d_err, 4);
+    ALLOC(m->d_slab_off, (size_t)2 * m->KL);  // radial sums of the other slabs (slab meshes)  // [0] error word, [2..3] budget of the pipeline waits (int64, 0: default)
     if (m->eff_prec == MP_PREC_FP64) {
         ALLOC(m->d_F64, (size_t)m->R * m->P);
         ALLOC(m->d_G64, (size_t)m->R * m->P);
@@ -549,6 +574,32 @@ mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edg
         if (st != MP_OK) return fail(st);
     }
     *out = m;
+    return MP_OK;
+}
+
+extern "C" {
+
+mp_status mp_mesh_create(const double *r_edges, int n_r, const double *theta_edges, int n_theta,
+                         const double *phi_edges, int n_phi, int l_max, double G, mp_precision prec, void *cuda_stream,
+                         mp_mesh **out)
+{
+    return create_mesh(r_edges, n_r, theta_edges, n_theta, phi_edges, n_phi, l_max, G, prec, cuda_stream, 0.0, out);
+}
+
+mp_status mp_mesh_create_slab(const double *r_edges, int n_r, int i0, int i1, const double *theta_edges,
+                              int n_theta, const double *phi_edges, int n_phi, int l_max, double G, mp_precision prec,
+                              void *cuda_stream, mp_mesh **out)
+{
+    g_detail[0] = 0;
+    if (!r_edges || n_r < 1) return set_error(MP_ERR_INVALID_ARG, "radial edges of the whole mesh are missing");
+    if (i0 < 0 || i1 > n_r || i1 <= i0) return set_error(MP_ERR_INVALID_ARG, "slab shells [%d, %d) outside [0, %d)", i0, i1, n_r);
+    if (!finite_increasing(r_edges, n_r) || r_edges[0] < 0.0)
+        return set_error(MP_ERR_INVALID_ARG, "radial edges must be finite, >= 0 and strictly increasing");
+    const double rmin = r_edges[0] > 0.0 ? r_edges[0] : r_edges[1];
+    mp_status st = create_mesh(r_edges + i0, i1 - i0, theta_edges, n_theta, phi_edges, n_phi, l_max, G, prec,
+                               cuda_stream, std::sqrt(rmin * r_edges[n_r]), out);
+    if (st != MP_OK) return st;
+    (*out)->slab = 1;
     return MP_OK;
 }
 
@@ -710,6 +761,47 @@ mp_status mp_mesh_synchronize(mp_mesh *m)
         if (err & DEV_ERR_NONFINITE) return set_error(MP_ERR_NONFINITE, "density holds NaN or infinity");
         return set_error(MP_ERR_CUDA, "device error word %d", err);
     }
+    return MP_OK;
+}
+
+mp_status mp_slab_moments(mp_mesh *m, double *totals_dev)
+{
+    if (!m || !totals_dev) return set_error(MP_ERR_INVALID_ARG, "NULL argument");
+    if (!m->rho) return set_error(MP_ERR_NOT_READY, "no density bound (mp_set_density)");
+    DeviceGuard dg(m->device);
+    mp_status st = run_moments(m, m->rho);
+    if (st != MP_OK) return st;
+    // the recurrences of this slab alone: its totals are M^R at its outer edge and M^I at its
+    // inner edge
+    m->use_slab_off = 0;
+    MP_TRY(launch_scan(m, 0));
+    const size_t kb = (size_t)m->KL * sizeof(double);
+    MP_TRY(cudaMemcpyAsync(totals_dev, m->d_MR + (size_t)m->n_r * m->KL, kb, cudaMemcpyDeviceToDevice, m->stream));
+    MP_TRY(cudaMemcpyAsync(totals_dev + m->KL, m->d_MI, kb, cudaMemcpyDeviceToDevice, m->stream));
+    m->slab_moments_ready = 1;
+    return MP_OK;
+}
+
+mp_status mp_slab_potential(mp_mesh *m, const double *outer_dev)
+{
+    if (!m || !outer_dev) return set_error(MP_ERR_INVALID_ARG, "NULL argument");
+    if (!m->slab_moments_ready) return set_error(MP_ERR_NOT_READY, "mp_slab_moments has not run on this slab");
+    DeviceGuard dg(m->device);
+    double *phi = m->phi_user;
+    if (!phi) {
+        mp_status st = ensure_phi_own(m);
+        if (st != MP_OK) return st;
+        phi = m->phi_own;
+    }
+    MP_TRY(cudaMemcpyAsync(m->d_slab_off, outer_dev, (size_t)2 * m->KL * sizeof(double), cudaMemcpyDeviceToDevice,
+                           m->stream));
+    m->use_slab_off = 1;
+    mp_status st = run_potential(m, phi);
+    m->use_slab_off = 0;
+    if (st != MP_OK) return st;
+    m->last_phi = phi;
+    m->solved = 1;
+    m->slab_moments_ready = 0;
     return MP_OK;
 }
 

@@ -160,6 +160,11 @@ struct mp_mesh {
     const double *last_phi = nullptr;  // device buffer holding the last solve's Phi
     int *d_err = nullptr;
     int solved = 0;
+    // radial-shell slab of a larger mesh: the other slabs' radial sums [2][K_L] (sum of
+    // W^R A below this slab, sum of W^I A above it), added to the recurrences when
+    // use_slab_off is set
+    int slab = 0, use_slab_off = 0, slab_moments_ready = 0;
+    double *d_slab_off = nullptr;
 
     // TMA descriptors, cached per bound pointer
     CUtensorMap tm_rho{}, tm_phi{};

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
                                              const double *__restrict__ GI, double *__restrict__ MR,
                                              double *__restrict__ MI, double *__restrict__ C,
                                              float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL,
-                                             const CbOut cbo)
+                                             const CbOut cbo, const double *__restrict__ off)
 {
     __shared__ double wt[2][NT / 32];
     // the next kernel's blocks may start (and copy their tables) while this one runs
@@ -107,6 +107,10 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
     }
     double mr, mi;
     block_exclusive_scans<NT>(sR, sI, mr, mi, wt);
+    if (off) {  // the sums of the slabs below (regular) and above (irregular) this one
+        mr += off[q];
+        mi += off[KL + q];
+    }
     // outward: edges i0 .. i1-1; the last thread also writes edge n_r
     for (int i = i0; i < i1; ++i) {
         MR[(size_t)i * KL + q] = mr;
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
                                                  const double *__restrict__ GI, double *__restrict__ MR,
                                                  double *__restrict__ MI, double *__restrict__ C,
                                                  float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL,
-                                                 const CbOut cbo)
+                                                 const CbOut cbo, const double *__restrict__ off)
 {
     __shared__ double wt[2][NT / 32];
     // the next kernel's blocks may start (and copy their tables) while this one runs
@@ -179,6 +183,10 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
     }
     double mr0, mi0;
     block_exclusive_scans<NT>(sR, sI, mr0, mi0, wt);
+    if (off) {  // the sums of the slabs below (regular) and above (irregular) this one
+        mr0 += off[q];
+        mi0 += off[KL + q];
+    }
     double er[CH + 1], ei[CH + 1];
     er[0] = mr0;
 #pragma unroll
@@ -219,7 +227,7 @@ __global__ void __launch_bounds__(4 * NT) k_scan_q4(const double *__restrict__ A
                                                     const double *__restrict__ GI, double *__restrict__ MR,
                                                     double *__restrict__ MI, double *__restrict__ C,
                                                     float *__restrict__ C32, float2 *__restrict__ C0, int n_r, int KL,
-                                                    const CbOut cbo)
+                                                    const CbOut cbo, const double *__restrict__ off)
 {
     constexpr int NW = 4 * NT / 32;
     __shared__ double wt[2][NW][4];
@@ -274,6 +282,10 @@ __global__ void __launch_bounds__(4 * NT) k_scan_q4(const double *__restrict__ A
     for (int w2_ = 0; w2_ < w; ++w2_) of += wt[0][w2_][sub];
     for (int w2_ = NW - 1; w2_ > w; --w2_) ob += wt[1][w2_][sub];
     if (!valid) return;
+    if (off) {  // the sums of the slabs below (regular) and above (irregular) this one
+        of += off[q];
+        ob += off[KL + q];
+    }
     double ei[CH + 1];
     ei[CH] = ob + eb;
 #pragma unroll
@@ -620,7 +632,7 @@ static void scan_reg_launch(mp_mesh *m, int want_f32)
 {
     launch_pdl(k_scan_reg<NT, CH>, dim3(m->KL), dim3(NT), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
                m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, want_f32 ? m->d_C0 : nullptr, m->n_r,
-               m->KL, cb_out(m, want_f32));
+               m->KL, cb_out(m, want_f32), m->use_slab_off ? (const double *)m->d_slab_off : nullptr);
 }
 
 // Shells per thread CH for NT threads per moment column; false when n_r > 16 NT.
@@ -673,7 +685,7 @@ static bool scan_q4_dispatch(mp_mesh *m, int want_f32)
     auto go = [&](auto kern) {
         launch_pdl(kern, dim3((m->KL + 3) / 4), dim3(512), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
                    m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, want_f32 ? m->d_C0 : nullptr, m->n_r,
-                   m->KL, cb_out(m, want_f32));
+                   m->KL, cb_out(m, want_f32), m->use_slab_off ? (const double *)m->d_slab_off : nullptr);
     };
     if (ch <= 4)
         go(k_scan_q4<128, 4>);
@@ -701,7 +713,8 @@ cudaError_t launch_scan(mp_mesh *m, int want_f32)
                                                                     m->d_MR, m->d_MI, m->d_C,
                                                                     want_f32 ? m->d_C32 : nullptr,
                                                                     want_f32 ? m->d_C0 : nullptr, m->n_r, m->KL,
-                                                                    cb_out(m, want_f32));
+                                                                    cb_out(m, want_f32),
+                                                                    m->use_slab_off ? (const double *)m->d_slab_off : nullptr);
     prof_end(m, "radial_scan", ev);
     return cudaGetLastError();
 }

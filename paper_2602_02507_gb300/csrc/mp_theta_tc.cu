@@ -56,7 +56,7 @@ constexpr int THREADS = (2 + CONV_WARPS) * 32;
 struct ThetaTcParams {
     const uint8_t *tab;              // order m >= 1: [n_kc][3 terms][Nm x 32] bf16, canonical K-major
     const unsigned long long *off;   // [L + 1] byte offset of order m's table
-    const float *F;                  // [n_r][P][ldF] (the m = 0 warps read row p = 0 of each shell)
+    const float *F;                  // [n_r][P][ldF] (the m = 0 kernel reads row p = 0 of each shell)
     const float *Ith32;              // [T][ldF]
     double *A;                       // [n_r][K_L]
     int *err;
@@ -64,53 +64,6 @@ struct ThetaTcParams {
     uint32_t stage_bytes;            // F boxes + the largest table chunk (the terms the products read)
     double scale;                    // 4 pi G
 };
-
-// Compensated (sum, error) pairs: TwoSum of the sums, errors added.
-__device__ __forceinline__ void kahan_pair_add(float &s, float &c, float s2, float c2)
-{
-    const float t = s + s2;
-    const float bv = t - s;
-    const float e = (s - (t - bv)) + (s2 - bv);
-    s = t;
-    c = c + c2 + e;
-}
-
-// m = 0 column of the theta contraction for one shell, one warp:
-//   A[i][l^2] = scale sum_j Ith[t(l,0)][j] F[i][0][j]
-// eight degrees at a time; each lane sums its polar cells (stride 32) with compensation,
-// the lanes' (sum, error) pairs meet in a compensated shuffle tree.
-__device__ void theta_m0_shell(const ThetaTcParams &prm, int i, int lane)
-{
-    const float *f = prm.F + (size_t)i * prm.P * prm.ldF;
-    for (int l0 = 0; l0 <= prm.L; l0 += 8) {
-        float s[8], c[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) s[e] = c[e] = 0.0f;
-        for (int j = lane; j < prm.n_t; j += 32) {
-            const float fj = __ldg(f + j);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int l = min(l0 + e, prm.L);
-                const float x = __ldg(prm.Ith32 + (size_t)tri(l, 0) * prm.ldF + j) * fj;
-                const float y = x - c[e];
-                const float t = s[e] + y;
-                c[e] = (t - s[e]) - y;
-                s[e] = t;
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) c[e] = -c[e];  // (sum, error) with sum + error the compensated total
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-                kahan_pair_add(s[e], c[e], __shfl_xor_sync(0xFFFFFFFFu, s[e], o), __shfl_xor_sync(0xFFFFFFFFu, c[e], o));
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-            if (lane == e && l0 + e <= prm.L)
-                prm.A[(size_t)i * prm.KL + (size_t)(l0 + e) * (l0 + e)] = prm.scale * f32_to_f64_alu(s[e] + c[e]);
-    }
-}
 
 template <int A_TERMS, int NPROD>
 __global__ void __launch_bounds__(thc::THREADS, 1) k_theta_tc(const __grid_constant__ CUtensorMap tmF,
@@ -550,26 +503,102 @@ __global__ void __launch_bounds__(gsc::THREADS, 1) k_gsynth_tc(const GsynthTcPar
 }
 
 // ---------------------------------------------------------------------------- m = 0 columns
-// (a2) m = 0: one warp per shell (theta_m0_shell), eight shells per block.
-__global__ void __launch_bounds__(256) k_theta_m0(const ThetaTcParams prm)
+// (a2) m = 0 as a register-tiled float32 GEMM with compensated sums:
+//   A[i][l^2] = scale sum_j Ith[t(l,0)][j] F[i][0][j]
+// Block (64 degrees, 16 shells) stages K chunks of 32 polar cells of both operands in
+// shared memory; thread (rg, cg) owns degrees rg + 16 a (a < 4) and shell cg; products are
+// summed over blocks of eight cells, block sums with Kahan compensation.
+constexpr int kM0Deg = 64, kM0Shells = 16, kM0K = 32, kM0Ld = kM0K + 4;
+
+__device__ __forceinline__ float dot4f(float4 a, float4 b, float acc)
 {
-    pdl_trigger();
-    pdl_wait();  // F comes from the previous kernel
-    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (i < prm.n_r) theta_m0_shell(prm, i, threadIdx.x & 31);
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, acc))));
 }
 
-// (d1) m = 0 in double-float: one thread per row (i, j), G0[row] = (hi, lo) of
-// sum_l (Ith[t(l,0)][j] / dmu_j) C[i][l^2].
-__global__ void __launch_bounds__(256) k_gsynth_m0(const float2 *__restrict__ C0, const float2 *__restrict__ Itc0,
-                                                   float *__restrict__ G0, long long R, int n_t, int L)
+__global__ void __launch_bounds__(256) k_theta_m0(const ThetaTcParams prm)
 {
+    __shared__ __align__(16) float sT[kM0Deg][kM0Ld];
+    __shared__ __align__(16) float sF[kM0Shells][kM0Ld];
+    pdl_trigger();
+    pdl_wait();  // F comes from the previous kernel
+    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+    const int i0 = blockIdx.x * kM0Shells, l0 = blockIdx.y * kM0Deg;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int j0 = 0; j0 < prm.n_t; j0 += kM0K) {
+        __syncthreads();  // the previous chunk is consumed
+        for (int e = tid; e < kM0Deg * (kM0K / 4); e += 256) {
+            const int r = e >> 3, q = e & 7, l = l0 + r, j = j0 + 4 * q;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (l <= prm.L && j < prm.ldF)
+                v = __ldg(reinterpret_cast<const float4 *>(prm.Ith32 + (size_t)tri(l, 0) * prm.ldF + j));
+            *reinterpret_cast<float4 *>(&sT[r][4 * q]) = v;
+        }
+        if (tid < kM0Shells * (kM0K / 4)) {
+            const int r = tid >> 3, q = tid & 7, i = i0 + r, j = j0 + 4 * q;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < prm.n_r && j < prm.ldF) v = __ldg(reinterpret_cast<const float4 *>(prm.F + (size_t)i * prm.P * prm.ldF + j));
+            *reinterpret_cast<float4 *>(&sF[r][4 * q]) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int jb = 0; jb < kM0K; jb += 8) {
+            const float4 f0 = *reinterpret_cast<const float4 *>(&sF[cg][jb]);
+            const float4 f1 = *reinterpret_cast<const float4 *>(&sF[cg][jb + 4]);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float4 t0 = *reinterpret_cast<const float4 *>(&sT[rg + 16 * a][jb]);
+                const float4 t1 = *reinterpret_cast<const float4 *>(&sT[rg + 16 * a][jb + 4]);
+                const float blk = dot4f(t1, f1, dot4f(t0, f0, 0.f));
+                const float y = blk - c[a];
+                const float t = s[a] + y;
+                c[a] = (t - s[a]) - y;
+                s[a] = t;
+            }
+        }
+    }
+    const int i = i0 + cg;
+    if (i >= prm.n_r) return;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int l = l0 + rg + 16 * a;
+        if (l <= prm.L) prm.A[(size_t)i * prm.KL + (size_t)l * l] = prm.scale * f32_to_f64_alu(s[a] - c[a]);
+    }
+}
+
+// (d1) m = 0 in double-float: G0[row] = (hi, lo) of sum_l (Ith[t(l,0)][j] / dmu_j) C[i][l^2]
+// for the rows (i, j) of a block of 128 polar cells and SB shells; the block's table slice
+// and coefficients sit in shared memory, thread (j, half) forms SB / 2 shells of cell j.
+__global__ void __launch_bounds__(256) k_gsynth_m0(const float2 *__restrict__ C0, const float2 *__restrict__ Itc0,
+                                                   float *__restrict__ G0, int n_r, int n_t, int L, int SB)
+{
+    extern __shared__ __align__(16) float2 sm0[];
+    float2 *sT = sm0;                          // [L + 1][128]
+    float2 *sC = sm0 + (size_t)(L + 1) * 128;  // [SB][L + 1]
+    const int tid = threadIdx.x;
+    const int j0 = blockIdx.x * 128, i0 = blockIdx.y * SB;
+    for (int e = tid; e < (L + 1) * 128; e += 256) {  // the static table, ahead of the wait
+        const int l = e >> 7, j = j0 + (e & 127);
+        sT[e] = j < n_t ? Itc0[(size_t)l * n_t + j] : make_float2(0.f, 0.f);
+    }
     pdl_trigger();
     pdl_wait();  // C0 comes from the previous kernel
-    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= R) return;
-    const int i = (int)(row / n_t), j = (int)(row - (long long)i * n_t);
-    *reinterpret_cast<float2 *>(G0 + 2 * row) = g0_double_float(Itc0 + j, n_t, C0 + (size_t)i * (L + 1), L);
+    for (int e = tid; e < SB * (L + 1); e += 256) {
+        const int i = i0 + e / (L + 1);
+        sC[e] = i < n_r ? C0[(size_t)i0 * (L + 1) + e] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int jj = tid & 127, half = tid >> 7, j = j0 + jj;
+    if (j >= n_t) return;
+    // this thread's shells in groups of four (SB is a multiple of 8): four chains in flight
+    for (int s0 = 4 * half; s0 < SB; s0 += 8) {
+        float2 g[4];
+        g0_double_float_n<4>(sT + jj, 128, sC + (size_t)s0 * (L + 1), L + 1, L, g);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + s0 + k;
+            if (i < n_r) *reinterpret_cast<float2 *>(G0 + 2 * ((size_t)i * n_t + j)) = g[k];
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------- tables
@@ -735,7 +764,8 @@ cudaError_t launch_theta_tc_tables(mp_mesh *m)
         for (cudaError_t r : {cudaFuncSetAttribute(k_theta_tc<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit),
                               cudaFuncSetAttribute(k_theta_tc<3, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit),
                               cudaFuncSetAttribute(k_gsynth_tc<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit),
-                              cudaFuncSetAttribute(k_gsynth_tc<3, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit)})
+                              cudaFuncSetAttribute(k_gsynth_tc<3, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit),
+                              cudaFuncSetAttribute(k_gsynth_m0, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit)})
             if (r != cudaSuccess) return r;
         attr_set = true;
     }
@@ -769,8 +799,9 @@ cudaError_t launch_theta_tc(mp_mesh *m)
     prm.bterms = pl.n_products == 3 ? 2 : 3;
     prm.stage_bytes = (uint32_t)(thc::F_BYTES + prm.bterms * pl.th_Nmax * 64);
     prm.scale = kFourPi * m->G;
-    // the m = 0 column first (CUDA cores, many small blocks), then the orders m >= 1
-    cudaError_t e = launch_pdl(k_theta_m0, dim3((m->n_r + 7) / 8), dim3(256), 0, m->stream, prm);
+    // the m = 0 column first (CUDA cores), then the orders m >= 1
+    cudaError_t e = launch_pdl(k_theta_m0, dim3((m->n_r + kM0Shells - 1) / kM0Shells, (m->L + kM0Deg) / kM0Deg),
+                               dim3(256), 0, m->stream, prm);
     if (e != cudaSuccess) return e;
     const int grid = std::min(pl.th_units, m->num_sms);
     if (pl.a_terms == 2)
@@ -799,8 +830,13 @@ cudaError_t launch_gsynth_tc(mp_mesh *m)
     prm.ns_s = pl.gs_ns_s;
     prm.bterms = pl.n_products == 3 ? 2 : 3;
     prm.stage_bytes = (uint32_t)(prm.bterms * gsc::T_TERM_BYTES + pl.a_terms * 2 * pl.gs_NS * 64);
-    cudaError_t e = launch_pdl(k_gsynth_m0, dim3((unsigned)((m->R + 255) / 256)), dim3(256), 0, m->stream,
-                               (const float2 *)m->d_C0, (const float2 *)m->d_Itc0, m->d_G0, m->R, m->n_t, m->L);
+    // the m = 0 column first (double-float on CUDA cores): 32 shells per block, or 8 when that
+    // leaves fewer than two blocks per SM
+    const int n_jb = (m->n_t + 127) / 128;
+    const int SB = (long long)n_jb * ((m->n_r + 31) / 32) >= 2LL * m->num_sms ? 32 : 8;
+    const size_t smem0 = ((size_t)(m->L + 1) * 128 + (size_t)SB * (m->L + 1)) * sizeof(float2);
+    cudaError_t e = launch_pdl(k_gsynth_m0, dim3(n_jb, (m->n_r + SB - 1) / SB), dim3(256), smem0, m->stream,
+                               (const float2 *)m->d_C0, (const float2 *)m->d_Itc0, m->d_G0, m->n_r, m->n_t, m->L, SB);
     if (e != cudaSuccess) return e;
     const int grid = std::min(pl.gs_units, m->num_sms);
     if (pl.a_terms == 2)

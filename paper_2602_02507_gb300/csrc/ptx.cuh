@@ -458,4 +458,36 @@ __device__ __forceinline__ float2 g0_double_float(const float2 *T, int t_stride,
     return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
 }
 
+// The same sum for NS coefficient rows c + k c_stride (k < NS) sharing the table column T:
+// NS independent accumulation chains in flight (a single chain is bound by the latency of
+// its dependent float32 operations).
+template <int NS>
+__device__ __forceinline__ void g0_double_float_n(const float2 *T, int t_stride, const float2 *c, int c_stride, int L,
+                                                  float2 (&out)[NS])
+{
+    float s[NS], e[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) s[k] = e[k] = 0.0f;
+    for (int l = 0; l <= L; ++l) {
+        const float2 t = T[(size_t)l * t_stride];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const float2 kk = c[(size_t)k * c_stride + l];
+            const float p = __fmul_rn(t.x, kk.x);
+            const float pe = fmaf(t.x, kk.x, -p);
+            const float cross = fmaf(t.x, kk.y, __fmul_rn(t.y, kk.x));
+            const float s2 = __fadd_rn(s[k], p);
+            const float bv = __fsub_rn(s2, s[k]);
+            const float se = __fadd_rn(__fsub_rn(s[k], __fsub_rn(s2, bv)), __fsub_rn(p, bv));
+            s[k] = s2;
+            e[k] = __fadd_rn(e[k], __fadd_rn(se, __fadd_rn(pe, cross)));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const float hi = __fadd_rn(s[k], e[k]);
+        out[k] = make_float2(hi, __fsub_rn(e[k], __fsub_rn(hi, s[k])));
+    }
+}
+
 }  // namespace mp

@@ -65,6 +65,9 @@ def load_library(path: str = LIB_PATH):
         "mp_mesh_synchronize": [vp],
         "mp_set_wait_budget": [vp, ctypes.c_longlong],
         "mp_set_theta_engine": [vp, i],
+        "mp_mesh_create_slab": [dp, i, i, i, dp, i, dp, i, i, d, i, vp, ctypes.POINTER(vp)],
+        "mp_slab_moments": [vp, vp],
+        "mp_slab_potential": [vp, vp],
         "mp_profile_enable": [vp, i],
         "mp_profile_read": [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i), dp, i, ctypes.POINTER(i)],
         "mp_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(vp)],
@@ -126,22 +129,33 @@ class Mesh:
     """A spherical mesh with its device tables (mp_mesh_create)."""
 
     def __init__(self, r_edges, theta_edges, phi_edges, l_max: int, G: float = 1.0,
-                 precision: str = "fp64", stream=None):
+                 precision: str = "fp64", stream=None, slab=None):
+        """slab=(i0, i1): shells [i0, i1) of the mesh with these radial edges
+        (mp_mesh_create_slab); the mesh's arrays then cover only those shells."""
         lib = load_library()
         self._lib = lib
-        self.r = np.ascontiguousarray(r_edges, dtype=np.float64)
+        r_all = np.ascontiguousarray(r_edges, dtype=np.float64)
+        self.r = r_all if slab is None else np.ascontiguousarray(r_all[slab[0]:slab[1] + 1])
         self.theta = np.ascontiguousarray(theta_edges, dtype=np.float64)
         self.phi = np.ascontiguousarray(phi_edges, dtype=np.float64)
         self.shape = (self.r.size - 1, self.theta.size - 1, self.phi.size - 1)
         self.l_max = int(l_max)
         self.precision = precision
+        self.slab = slab
         self._stream = stream
         handle = ctypes.c_void_p()
-        st = lib.mp_mesh_create(_dptr(self.r), self.shape[0], _dptr(self.theta), self.shape[1],
-                                _dptr(self.phi), self.shape[2], self.l_max, float(G),
-                                PRECISIONS[precision], ctypes.c_void_p(_stream_handle(stream)),
-                                ctypes.byref(handle))
-        _check(st, "mp_mesh_create")
+        if slab is None:
+            st = lib.mp_mesh_create(_dptr(self.r), self.shape[0], _dptr(self.theta), self.shape[1],
+                                    _dptr(self.phi), self.shape[2], self.l_max, float(G),
+                                    PRECISIONS[precision], ctypes.c_void_p(_stream_handle(stream)),
+                                    ctypes.byref(handle))
+            _check(st, "mp_mesh_create")
+        else:
+            st = lib.mp_mesh_create_slab(_dptr(r_all), r_all.size - 1, int(slab[0]), int(slab[1]), _dptr(self.theta),
+                                         self.shape[1], _dptr(self.phi), self.shape[2], self.l_max, float(G),
+                                         PRECISIONS[precision], ctypes.c_void_p(_stream_handle(stream)),
+                                         ctypes.byref(handle))
+            _check(st, "mp_mesh_create_slab")
         self._h = handle
         self._rho = None
         self._phi = None
@@ -246,6 +260,17 @@ class Mesh:
 
     def synchronize(self):
         _check(self._lib.mp_mesh_synchronize(self._h), "mp_mesh_synchronize")
+
+    def slab_moments(self, totals):
+        """Moments of the bound density and this slab's radial totals into totals
+        ([2 * K_L] CUDA float64: sums of W^R A and of W^I A over its shells)."""
+        _check(self._lib.mp_slab_moments(self._h, ctypes.c_void_p(_tensor_ptr(totals, 2 * self.n_moments, "totals"))),
+               "mp_slab_moments")
+
+    def slab_potential(self, outer):
+        """Potential of this slab given the other slabs' sums outer ([2 * K_L] CUDA float64)."""
+        _check(self._lib.mp_slab_potential(self._h, ctypes.c_void_p(_tensor_ptr(outer, 2 * self.n_moments, "outer"))),
+               "mp_slab_potential")
 
     def set_theta_engine(self, engine: str):
         """Engine of the theta stages on the split path: "auto", "tensor" (tcgen05 for the
