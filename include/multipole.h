@@ -355,8 +355,8 @@ MP_API mp_status mp_probe_rates(double *fp64_tflops, double *cvt_f64_f32_per_s);
  * Angular moments (step (a), in float64) of rho_dev into ang_dev [n_r][K_L],
  * using the mesh's tables, without allocating any device memory.  The paper
  * has no counterpart: this entry point serves callers that cannot allocate at
- * the point of use -- code running inside a CUDA graph capture, real-time loops
- * with a fixed memory budget, or plug-ins whose host owns every allocation.
+ * the point of use -- real-time loops with a memory budget fixed up front, or
+ * plug-ins whose host application owns every device allocation.
  * Its only intermediate array lives in a fixed device array of
  * MP_NOALLOC_SCRATCH_DOUBLES float64 values (32 MiB) that every GPU loading
  * this library holds until the process exits; meshes with
@@ -366,7 +366,9 @@ MP_API mp_status mp_probe_rates(double *fp64_tflops, double *cvt_f64_f32_per_s);
  * before any stream capture.  Work is enqueued on the mesh's stream; calls
  * whose work overlaps on the GPU share the array and race.  rho_dev and
  * ang_dev are device pointers owned by the caller; the moments of the mesh's
- * own solves are not touched.
+ * own solves are not touched.  A NaN or infinite density is recorded in the
+ * mesh's device error word and reported as MP_ERR_NONFINITE by the next
+ * mp_mesh_synchronize().
  */
 #define MP_NOALLOC_SCRATCH_DOUBLES (4u << 20)
 MP_API mp_status mp_moments_noalloc(const mp_mesh *mesh, const double *rho_dev, double *ang_dev);

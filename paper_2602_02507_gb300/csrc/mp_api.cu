@@ -351,6 +351,10 @@ static mp_status plan_split(mp_mesh *m)
         }
     }
     pl.n_nc = (m->n_p + pl.NC - 1) / pl.NC;
+    // projection accumulators per tile: as many as tensor memory holds (up to 4), each chain of
+    // float32 additions in the tensor core that many times shorter
+    pl.proj_nacc_max = std::max(1, std::min(std::min(4, 256 / pl.Npad), pl.n_kc));
+    pl.proj_nacc = pl.proj_nacc_max;
     pl.proj_ctas = m->num_sms;
     pl.synth_ctas = m->num_sms;
     if (split_smem_limits(m) != 0)
@@ -524,6 +528,7 @@ static mp_status create_mesh(const double *r_edges, int n_r, const double *theta
             ALLOC(m->d_tabTh, th_bytes);
             ALLOC(m->d_tabGs, gs_bytes);
             ALLOC(m->d_Cb, cb_bytes);
+            m->cb_bytes_alloc = cb_bytes;
             ALLOC(m->d_th_off, (size_t)(l_max + 1));
             ALLOC(m->d_gs_off, (size_t)(l_max + 1));
             ALLOC(m->d_cb_off, (size_t)(l_max + 1));
@@ -911,10 +916,16 @@ mp_status mp_profile_read(mp_mesh *m, const char **names, int *launches, double 
 
 // ---------------------------------------------------------------- batches
 struct mp_batch {
+#ifndef MP_BATCH_BRANCHES
+#define MP_BATCH_BRANCHES 4
+#endif
+    static constexpr int kBranches = MP_BATCH_BRANCHES;  // parallel chains of meshes in the captured graph
     std::vector<mp_mesh *> meshes;
     std::vector<const void *> bound;  // rho / phi pointers the graph was captured with
     cudaStream_t stream = nullptr;    // caller's stream (that of the first mesh)
     cudaStream_t cap = nullptr;       // private stream the graph is captured on and runs on
+    cudaStream_t side[kBranches] = {};                        // capture streams of the branches
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -946,14 +957,17 @@ mp_status mp_batch_create(mp_mesh *const *meshes, int count, mp_batch **out)
     b->stream = meshes[0]->stream;
     b->device = meshes[0]->device;
     DeviceGuard dg(b->device);
-    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
-        mp_status st = cuda_status(cudaGetLastError(), "batch stream/events");
-        if (b->cap) cudaStreamDestroy(b->cap);
-        if (b->ev_in) cudaEventDestroy(b->ev_in);
-        delete b;
-        return st == MP_OK ? set_error(MP_ERR_CUDA, "batch stream/events") : st;
+    bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < mp_batch::kBranches && ok; ++k)
+        ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        mp_status st = cuda_status(cudaGetLastError(), "batch streams/events");
+        mp_batch_destroy(b);
+        return st == MP_OK ? set_error(MP_ERR_CUDA, "batch streams/events") : st;
     }
     *out = b;
     return MP_OK;
@@ -982,10 +996,27 @@ mp_status mp_batch_solve(mp_batch *b)
         // eager first pass (builds TMA descriptors), then capture the batch
         std::vector<cudaStream_t> saved;
         std::vector<int> prof;
-        for (mp_mesh *m : b->meshes) {
+        // the meshes go to kBranches parallel chains of the graph, largest first, each to the
+        // chain with the fewest cells so far: small meshes then share the SMs instead of each
+        // leaving most of them idle between its kernels
+        const int nb = std::min<int>(mp_batch::kBranches, (int)b->meshes.size());
+        std::vector<int> order(b->meshes.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return (double)b->meshes[x]->N * b->meshes[x]->KL > (double)b->meshes[y]->N * b->meshes[y]->KL;
+        });
+        std::vector<double> load(nb, 0.0);
+        std::vector<int> branch(b->meshes.size(), 0);
+        for (int i : order) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            branch[i] = k;
+            load[k] += (double)b->meshes[i]->N * b->meshes[i]->KL;
+        }
+        for (size_t i = 0; i < b->meshes.size(); ++i) {
+            mp_mesh *m = b->meshes[i];
             saved.push_back(m->stream);
             prof.push_back(m->profiling);
-            m->stream = b->cap;
+            m->stream = b->side[branch[i]];
             m->profiling = 0;
         }
         auto restore = [&] {
@@ -1001,10 +1032,20 @@ mp_status mp_batch_solve(mp_batch *b)
             restore();
             return cuda_status(e, "cudaStreamBeginCapture");
         }
-        for (mp_mesh *m : b->meshes) {
+        // fork: every branch starts after the capture stream's start, and the capture stream
+        // waits for every branch at the end
+        e = cudaEventRecord(b->fork, b->cap);
+        for (int k = 0; k < nb && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+        if (e != cudaSuccess) st = cuda_status(e, "batch fork");
+        for (size_t i = 0; i < b->meshes.size() && st == MP_OK; ++i) {
+            mp_mesh *m = b->meshes[order[i]];
             m->last_phi = m->phi_user ? m->phi_user : m->phi_own;
             st = run_solve(m, m->rho, m->phi_user ? m->phi_user : m->phi_own);
-            if (st != MP_OK) break;
+        }
+        for (int k = 0; k < nb; ++k) {
+            cudaError_t e2 = cudaEventRecord(b->join[k], b->side[k]);
+            if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(b->cap, b->join[k], 0);
+            if (e2 != cudaSuccess && st == MP_OK) st = cuda_status(e2, "batch join");
         }
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(b->cap, &graph);
@@ -1035,13 +1076,17 @@ mp_status mp_batch_destroy(mp_batch *b)
 {
     if (!b) return set_error(MP_ERR_INVALID_ARG, "batch is NULL");
     DeviceGuard dg(b->device);
-    cudaStreamSynchronize(b->stream);
-    cudaStreamSynchronize(b->cap);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->cap) cudaStreamSynchronize(b->cap);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    cudaEventDestroy(b->ev_in);
-    cudaEventDestroy(b->ev_out);
-    cudaStreamDestroy(b->cap);
+    for (cudaEvent_t e : {b->ev_in, b->ev_out, b->fork})
+        if (e) cudaEventDestroy(e);
+    for (int k = 0; k < mp_batch::kBranches; ++k) {
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    }
+    if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return MP_OK;
 }
@@ -1053,6 +1098,47 @@ static std::string tune_key(const mp_mesh *m)
     k << m->n_r << ' ' << m->n_t << ' ' << m->n_p << ' ' << m->L << ' ' << m->eff_prec;
     return k.str();
 }
+
+}  // extern "C"
+
+// One point of the tuner's search space.
+struct TuneCfg {
+    int ns_s, ns_b, sw, br, tc, gs_ns, nacc;
+};
+
+static TuneCfg current_cfg(const mp_mesh *m)
+{
+    const SplitPlan &p = m->plan;
+    return {p.ns_s, p.ns_b, p.scan_threads, p.proj_b_resident, p.use_theta_tc, p.gs_NS, p.proj_nacc};
+}
+
+// Whether a configuration (a cache line, or a tuner candidate) fits this mesh's plan.
+static bool cfg_fits(const mp_mesh *m, const TuneCfg &c)
+{
+    const SplitPlan &p = m->plan;
+    if (!(c.sw == 64 || c.sw == 128 || c.sw == 256)) return false;
+    if (m->eff_prec == MP_PREC_FP64) return true;
+    // the density ring is even (the two converter groups alternate over its slots)
+    return c.ns_s >= 2 && !(c.ns_s & 1) && c.ns_s <= p.ns_s_max && c.ns_b >= 1 && c.ns_b <= p.ns_b_max &&
+           (c.br ? p.proj_res_ok : p.proj_ring_ok) && (c.tc == 0 || p.theta_tc_ok) &&
+           (c.gs_ns == 8 || c.gs_ns == 16 || c.gs_ns == 32) && c.nacc >= 1 && c.nacc <= p.proj_nacc_max;
+}
+
+static mp_status apply_cfg(mp_mesh *m, const TuneCfg &c)
+{
+    SplitPlan &p = m->plan;
+    p.ns_s = c.ns_s;
+    p.ns_b = c.ns_b;
+    p.scan_threads = c.sw;
+    p.proj_b_resident = c.br;
+    p.use_theta_tc = c.tc;
+    p.proj_nacc = c.nacc;
+    if (p.theta_tc_ok && c.gs_ns != p.gs_NS) MP_TRY(set_gsynth_ns(m, c.gs_ns));
+    drop_graph(m);
+    return MP_OK;
+}
+
+extern "C" {
 
 mp_status mp_autotune(mp_mesh *m, const char *cache_path)
 {
@@ -1066,23 +1152,16 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
         std::string line;
         while (std::getline(f, line)) {
             std::istringstream is(line);
-            int a, b, c, d, e, ns_s, ns_b, sw, br, tc;
-            if (is >> a >> b >> c >> d >> e >> ns_s >> ns_b >> sw >> br >> tc) {
+            int a, b, c, d, e;
+            TuneCfg t;
+            if (is >> a >> b >> c >> d >> e >> t.ns_s >> t.ns_b >> t.sw >> t.br >> t.tc >> t.gs_ns >> t.nacc) {
                 std::ostringstream k;
                 k << a << ' ' << b << ' ' << c << ' ' << d << ' ' << e;
-                // a line that does not fit this plan's reserved memory (or an odd density
-                // ring, which the converter groups cannot share) is not used
-                const bool fits = ns_s >= 2 && !(ns_s & 1) && ns_s <= m->plan.ns_s_max && ns_b >= 1 &&
-                                  ns_b <= m->plan.ns_b_max && (sw == 64 || sw == 128 || sw == 256) &&
-                                  (tc == 0 || m->plan.theta_tc_ok);
-                if (k.str() == key && fits) {
-                    m->plan.ns_s = ns_s;
-                    m->plan.ns_b = ns_b;
-                    m->plan.scan_threads = sw;
-                    m->plan.proj_b_resident = br ? m->plan.proj_res_ok : !m->plan.proj_ring_ok;
-                    m->plan.use_theta_tc = tc;
+                // a line that does not fit this plan's reserved memory is not used
+                if (k.str() == key && cfg_fits(m, t)) {
+                    mp_status st = apply_cfg(m, t);
+                    if (st != MP_OK) return st;
                     m->tuned_candidates = 0;
-                    drop_graph(m);
                     return MP_OK;
                 }
             }
@@ -1095,76 +1174,89 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
         phi = m->phi_own;
     }
     const SplitPlan base = m->plan;
-    struct Cand {
-        int ns_s, ns_b, sw, br, tc;
-    };
-    std::vector<Cand> cands;
-    const int sws[] = {64, 128, 256};
-    if (m->eff_prec == MP_PREC_FP64) {
-        for (int sw : sws) cands.push_back({base.ns_s, base.ns_b, sw, 0, 0});
-    } else {
-        // the synthesis table ring depth only matters when the table is not resident
-        const int ns_b_lo = base.b_resident ? base.ns_b_max : 2;
-        // even density-ring depths only (the converter groups alternate over its slots); the
-        // theta stages on the tensor cores or on the CUDA cores
-        for (int tc = 0; tc <= base.theta_tc_ok; ++tc)
-            for (int ns_s = 2; ns_s <= base.ns_s_max; ns_s += 2)
-                for (int ns_b = ns_b_lo; ns_b <= base.ns_b_max; ++ns_b)
-                    for (int br = 0; br <= 1; ++br)
-                        if (br ? base.proj_res_ok : base.proj_ring_ok)
-                            for (int sw : sws) cands.push_back({ns_s, ns_b, sw, br, tc});
-    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int saved_prof = m->profiling;
     m->profiling = 0;
-    float best = FLT_MAX;
-    Cand best_c = {base.ns_s, base.ns_b, base.scan_threads, base.proj_b_resident, base.use_theta_tc};
-    mp_status st = MP_OK;
-    for (const Cand &c : cands) {
-        m->plan.ns_s = c.ns_s;
-        m->plan.ns_b = c.ns_b;
-        m->plan.scan_threads = c.sw;
-        m->plan.proj_b_resident = c.br;
-        m->plan.use_theta_tc = c.tc;
-        st = run_solve(m, m->rho, phi);  // warm-up
-        if (st != MP_OK) break;
+    int timed = 0;
+    // device time of three solves (after one warm-up) in configuration c
+    auto time_cfg = [&](const TuneCfg &c, float *ms) -> mp_status {
+        mp_status st = apply_cfg(m, c);
+        if (st != MP_OK) return st;
+        st = run_solve(m, m->rho, phi);
+        if (st != MP_OK) return st;
         cudaEventRecord(e0, m->stream);
-        for (int it = 0; it < 3; ++it) {
-            st = run_solve(m, m->rho, phi);
-            if (st != MP_OK) break;
-        }
+        for (int it = 0; it < 3 && st == MP_OK; ++it) st = run_solve(m, m->rho, phi);
+        if (st != MP_OK) return st;
         cudaEventRecord(e1, m->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            st = cuda_status(cudaGetLastError(), "autotune timing");
-            break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_status(cudaGetLastError(), "autotune timing");
+        cudaEventElapsedTime(ms, e0, e1);
+        ++timed;
+        return MP_OK;
+    };
+    // Coordinate descent over the choices, most consequential first: the theta engine, the
+    // theta synthesis shells per unit (a tile shape: N = 2 NS), the projection accumulators
+    // per tile, the density ring depth with the table residency, the synthesis table ring,
+    // the threads per moment column of the recurrences.  Each dimension is swept with the
+    // others held at the best so far.
+    TuneCfg best = current_cfg(m);
+    float best_ms = FLT_MAX;
+    mp_status st = time_cfg(best, &best_ms);
+    auto sweep = [&](const std::vector<TuneCfg> &cands) {
+        for (const TuneCfg &c : cands) {
+            if (st != MP_OK) return;
+            if (!cfg_fits(m, c)) continue;
+            float ms = 0.0f;
+            st = time_cfg(c, &ms);
+            if (st == MP_OK && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
         }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_c = c;
+    };
+    std::vector<TuneCfg> cands;
+    if (m->eff_prec != MP_PREC_FP64) {
+        cands.clear();
+        for (int tc = 0; tc <= base.theta_tc_ok; ++tc) cands.push_back({best.ns_s, best.ns_b, best.sw, best.br, tc, best.gs_ns, best.nacc});
+        sweep(cands);
+        if (best.tc) {
+            cands.clear();
+            for (int ns : {8, 16, 32}) cands.push_back({best.ns_s, best.ns_b, best.sw, best.br, best.tc, ns, best.nacc});
+            sweep(cands);
+        }
+        cands.clear();
+        for (int na = 1; na <= base.proj_nacc_max; ++na) cands.push_back({best.ns_s, best.ns_b, best.sw, best.br, best.tc, best.gs_ns, na});
+        sweep(cands);
+        cands.clear();
+        for (int ns_s = 2; ns_s <= base.ns_s_max; ns_s += 2)
+            for (int br = 0; br <= 1; ++br) cands.push_back({ns_s, best.ns_b, best.sw, br, best.tc, best.gs_ns, best.nacc});
+        sweep(cands);
+        if (!base.b_resident) {
+            cands.clear();
+            for (int ns_b = 2; ns_b <= base.ns_b_max; ++ns_b) cands.push_back({best.ns_s, ns_b, best.sw, best.br, best.tc, best.gs_ns, best.nacc});
+            sweep(cands);
         }
     }
+    cands.clear();
+    for (int sw : {64, 128, 256}) cands.push_back({best.ns_s, best.ns_b, sw, best.br, best.tc, best.gs_ns, best.nacc});
+    sweep(cands);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     m->profiling = saved_prof;
-    m->plan.ns_s = best_c.ns_s;
-    m->plan.ns_b = best_c.ns_b;
-    m->plan.scan_threads = best_c.sw;
-    m->plan.proj_b_resident = best_c.br;
-    m->plan.use_theta_tc = best_c.tc;
-    m->tuned_candidates = (int)cands.size();
-    drop_graph(m);
+    m->tuned_candidates = timed;
     if (st != MP_OK) {
         m->plan = base;
+        if (base.theta_tc_ok) set_gsynth_ns(m, base.gs_NS);
+        drop_graph(m);
         return st;
     }
+    st = apply_cfg(m, best);
+    if (st != MP_OK) return st;
     if (cache_path) {
         std::ofstream f(cache_path, std::ios::app);
-        f << key << ' ' << best_c.ns_s << ' ' << best_c.ns_b << ' ' << best_c.sw << ' ' << best_c.br << ' '
-          << best_c.tc << '\n';
+        f << key << ' ' << best.ns_s << ' ' << best.ns_b << ' ' << best.sw << ' ' << best.br << ' ' << best.tc << ' '
+          << best.gs_ns << ' ' << best.nacc << '\n';
     }
     return mp_mesh_synchronize(m);
 }

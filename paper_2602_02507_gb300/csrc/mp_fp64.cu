@@ -106,6 +106,19 @@ cudaError_t launch_fp64_project(mp_mesh *m, const double *rho)
     return cudaGetLastError();
 }
 
+cudaError_t launch_fp64_moments_into(const mp_mesh *m, const double *rho, double *F, double *A)
+{
+    const long long blocks = (m->R + kRowsPerBlock - 1) / kRowsPerBlock;
+    const size_t smem = (size_t)kRowsPerBlock * m->n_p * sizeof(double);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k64_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k64_project<<<(unsigned)blocks, 256, smem, m->stream>>>(rho, m->d_Iph, F, m->R, m->n_p, m->P, m->d_err);
+    k64_theta<<<m->n_r, 256, 0, m->stream>>>(F, m->d_Ith, A, m->n_t, m->L, m->KL, m->P, kFourPi * m->G);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fp64_theta(mp_mesh *m)
 {
     cudaEvent_t ev;

@@ -46,6 +46,8 @@ struct SplitPlan {
     int ns_a = 2;         // synthesis: A-operand stages
     int b_resident = 0;   // synthesis: whole table held in shared memory
     int stg_bufs = 2;     // synthesis: TMA store staging boxes per epilogue warp
+    int proj_nacc = 1;    // projection: accumulators per tile (K chunks dealt round-robin)
+    int proj_nacc_max = 1;
     int scan_threads = 128;  // radial recurrences: threads (shell chunks) per moment column
     // theta stages on the tensor cores (orders m >= 1; mp_theta_tc.cu): possible for this mesh
     // (tables built), in use, and the choice the rule makes
@@ -142,6 +144,7 @@ struct mp_mesh {
     uint8_t *d_tabTh = nullptr, *d_tabGs = nullptr, *d_Cb = nullptr;
     unsigned long long *d_th_off = nullptr, *d_gs_off = nullptr, *d_cb_off = nullptr;
     CUtensorMap tm_F{};
+    size_t cb_bytes_alloc = 0;
     uint8_t *d_tabB = nullptr;    // projection B operand, bf16 x 3 terms, canonical layout
     uint8_t *d_tabT = nullptr;    // synthesis B operand, bf16 x 3 terms, canonical layout
     size_t tabB_chunk_bytes = 0, tabT_chunk_bytes = 0;
@@ -192,6 +195,10 @@ struct mp_mesh {
     size_t device_bytes = 0;
 };
 
+#ifndef MP_PDL_ALLOWED
+#define MP_PDL_ALLOWED 1
+#endif
+
 namespace mp {
 
 // error detail of the calling host thread
@@ -212,7 +219,7 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[0].val.programmaticStreamSerializationAllowed = MP_PDL_ALLOWED;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
@@ -225,6 +232,8 @@ cudaError_t launch_split_tables(mp_mesh *m);
 cudaError_t launch_fp64_project(mp_mesh *m, const double *rho);
 cudaError_t launch_fp64_theta(mp_mesh *m);
 cudaError_t launch_fp64_synth(mp_mesh *m, double *phi);
+// step (a) in float64 with caller-provided workspace F [R][2L+1] and output A [n_r][K_L]
+cudaError_t launch_fp64_moments_into(const mp_mesh *m, const double *rho, double *F, double *A);
 
 // ---- shared radial recurrences ----
 cudaError_t launch_scan(mp_mesh *m, int want_f32);
@@ -241,6 +250,8 @@ int split_smem_limits(mp_mesh *m);  // 0 when the plan fits, else an error
 bool plan_theta_tc(mp_mesh *m, std::vector<unsigned long long> &th_off, size_t &th_bytes,
                    std::vector<unsigned long long> &gs_off, size_t &gs_bytes, std::vector<unsigned long long> &cb_off,
                    size_t &cb_bytes);
+bool gsynth_plan_ns(mp_mesh *m, int ns, std::vector<unsigned long long> &cb_off, size_t &cb_bytes);
+cudaError_t set_gsynth_ns(mp_mesh *m, int ns);
 cudaError_t launch_theta_tc_tables(mp_mesh *m);
 cudaError_t launch_theta_tc(mp_mesh *m);   // theta contraction, m >= 1
 cudaError_t launch_gsynth_tc(mp_mesh *m);  // theta synthesis, m >= 1

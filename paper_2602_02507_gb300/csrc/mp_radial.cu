@@ -469,7 +469,10 @@ __global__ void __launch_bounds__(1024, 1) k32_theta_pipe(const float *__restric
         const float *fb = sF + (size_t)b * shell_floats;
         // whole warps run the loop together (the lane partials meet by shuffles)
         for (int wb = tid - lane; wb < n_work; wb += nthr) item(fb, A + (size_t)i * KL, wb + lane);
-        __syncthreads();  // buffer b consumed
+        // buffer b consumed: its plain reads are ordered before the bulk copy (async proxy) that
+        // refills it
+        fence_proxy_async_smem();
+        __syncthreads();
         if (tid == 0 && i + 2 * (int)gridDim.x < n_r) issue(i + 2 * gridDim.x, b);
     }
     if (!ok && tid == 0) {
@@ -751,12 +754,7 @@ static cudaError_t theta_cuda_cores(mp_mesh *m, int orders_hi)
 cudaError_t launch_split_theta(mp_mesh *m)
 {
     cudaEvent_t ev;
-    if (m->plan.use_theta_tc) {
-        prof_begin(m, "split_theta_contract_tc", &ev);
-        cudaError_t e = launch_theta_tc(m);
-        prof_end(m, "split_theta_contract_tc", ev);
-        return e;
-    }
+    if (m->plan.use_theta_tc) return launch_theta_tc(m);  // profiles its two kernels itself
     prof_begin(m, "split_theta_contract", &ev);
     cudaError_t e = theta_cuda_cores(m, m->L);
     prof_end(m, "split_theta_contract", ev);

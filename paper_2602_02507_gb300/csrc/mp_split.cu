@@ -922,6 +922,9 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
             ok = warp_all(mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err));
             if (!ok) break;
             const float2 g0 = reinterpret_cast<const float2 *>(sA + (size_t)ra.idx * a_stage + prm.a_bytes)[row];
+            // the stage is refilled by the bulk-copy engine (the async proxy): the m = 0 values just
+            // read must be ordered before that write, or a late read returns the next unit's values
+            fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&a_empty[ra.idx]));
             const long long box_row = (long long)tile * kBM + qd * 32;
@@ -1215,7 +1218,7 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho)
     if ((prm.ns_s & 1) || (prm.ns_o & 1) || prm.ns_s < 2 || prm.ns_o < 2) return cudaErrorInvalidValue;
     prm.bchunk = (uint32_t)(3 * pl.Npad * proj::BK * 2);
     prm.bload = (uint32_t)(proj_b_terms(pl) * pl.Npad * proj::BK * 2);
-    prm.nacc = std::max(1, std::min(std::min(4, 256 / pl.Npad), pl.n_kc));
+    prm.nacc = std::max(1, std::min(pl.proj_nacc, pl.proj_nacc_max));
     prm.b_resident = pl.proj_b_resident;
     prm.ns_b = pl.ns_s;
     const int grid = std::min(prm.n_tiles, pl.proj_ctas);
@@ -1236,9 +1239,7 @@ cudaError_t launch_split_synth(mp_mesh *m, double *phi)
     (void)phi;
     cudaEvent_t ev;
     if (m->plan.use_theta_tc) {
-        prof_begin(m, "split_theta_synth_tc", &ev);
-        cudaError_t e = launch_gsynth_tc(m);
-        prof_end(m, "split_theta_synth_tc", ev);
+        cudaError_t e = launch_gsynth_tc(m);  // profiles its two kernels itself
         if (e != cudaSuccess) return e;
         return launch_phi_synth(m);
     }

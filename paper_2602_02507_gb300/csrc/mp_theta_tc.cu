@@ -519,7 +519,8 @@ __global__ void __launch_bounds__(256) k_theta_m0(const ThetaTcParams prm)
 {
     __shared__ __align__(16) float sT[kM0Deg][kM0Ld];
     __shared__ __align__(16) float sF[kM0Shells][kM0Ld];
-    pdl_trigger();
+    // no early trigger: the tensor-core kernel that follows holds one CTA of shared memory
+    // per SM, which would leave this kernel's later blocks no room
     pdl_wait();  // F comes from the previous kernel
     const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
     const int i0 = blockIdx.x * kM0Shells, l0 = blockIdx.y * kM0Deg;
@@ -580,8 +581,7 @@ __global__ void __launch_bounds__(256) k_gsynth_m0(const float2 *__restrict__ C0
         const int l = e >> 7, j = j0 + (e & 127);
         sT[e] = j < n_t ? Itc0[(size_t)l * n_t + j] : make_float2(0.f, 0.f);
     }
-    pdl_trigger();
-    pdl_wait();  // C0 comes from the previous kernel
+    pdl_wait();  // C0 comes from the previous kernel (no early trigger: see k_theta_m0)
     for (int e = tid; e < SB * (L + 1); e += 256) {
         const int i = i0 + e / (L + 1);
         sC[e] = i < n_r ? C0[(size_t)i0 * (L + 1) + e] : make_float2(0.f, 0.f);
@@ -676,6 +676,44 @@ size_t gsynth_tc_smem(const SplitPlan &pl)
     return 128 + (size_t)pl.gs_ns_s * stage + 512;
 }
 
+// Theta synthesis with NS shells per unit: fills pl.gs_* and the per-order offsets of the
+// coefficient terms the radial recurrences write (false when the stages do not fit).
+bool gsynth_plan_ns(mp_mesh *m, int ns, std::vector<unsigned long long> &cb_off, size_t &cb_bytes)
+{
+    SplitPlan &pl = m->plan;
+    const int L = m->L;
+    pl.gs_NS = ns;
+    pl.gs_n_sg = (m->n_r + ns - 1) / ns;
+    pl.gs_units = pl.gs_n_jb * pl.gs_n_sg * pl.gs_n_mg;
+    pl.gs_ns_s = 4;
+    while (pl.gs_ns_s > 2 && gsynth_tc_smem(pl) > (size_t)kSmemLimit) --pl.gs_ns_s;
+    if (gsynth_tc_smem(pl) > (size_t)kSmemLimit) return false;
+    pl.gs_smem = (int)gsynth_tc_smem(pl);
+    cb_off.assign(L + 1, 0);
+    cb_bytes = 0;
+    for (int mm = 1; mm <= L; ++mm) {
+        const int n_kcm = (L + 1 - mm + 31) / 32;
+        cb_off[mm] = cb_bytes;
+        cb_bytes += (size_t)pl.gs_n_sg * n_kcm * pl.a_terms * 2 * ns * 64;
+    }
+    return true;
+}
+
+// Switches a mesh's theta synthesis to NS shells per unit (8, 16 or 32): new coefficient
+// offsets, and the coefficient buffer cleared (its padding must read as zeros).  Waits for
+// the mesh's stream.
+cudaError_t set_gsynth_ns(mp_mesh *m, int ns)
+{
+    std::vector<unsigned long long> cb_off;
+    size_t cb_bytes = 0;
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return e;
+    if (!gsynth_plan_ns(m, ns, cb_off, cb_bytes) || cb_bytes > m->cb_bytes_alloc) return cudaErrorInvalidValue;
+    e = cudaMemcpy(m->d_cb_off, cb_off.data(), cb_off.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(m->d_Cb, 0, m->cb_bytes_alloc, m->stream);
+}
+
 // Sizes of the tensor-core theta stages; fills pl.th_* / pl.gs_* and the table offsets.
 // Returns false when they do not apply (l_max = 0: only the m = 0 column exists).
 bool plan_theta_tc(mp_mesh *m, std::vector<unsigned long long> &th_off, size_t &th_bytes,
@@ -703,31 +741,28 @@ bool plan_theta_tc(mp_mesh *m, std::vector<unsigned long long> &th_off, size_t &
         th_bytes += (size_t)pl.th_n_kc * 3 * round16(L + 1 - mm) * 64;
     }
     // (d1): 128 polar cells x NS shells x 4 orders per unit; NS the widest of 32 / 16 / 8 that
-    // still gives every SM two units
+    // still gives every SM two units (mp_autotune may choose another; the coefficient buffer
+    // is sized for the widest)
     pl.gs_n_jb = (m->n_t + 127) / 128;
     pl.gs_n_mg = (L + gsc::ORDERS - 1) / gsc::ORDERS;
-    pl.gs_NS = 8;
-    for (int ns = 32; ns >= 16; ns /= 2) {
-        const long long units = (long long)pl.gs_n_jb * ((m->n_r + ns - 1) / ns) * pl.gs_n_mg;
+    int ns = 8;
+    for (int c = 32; c >= 16; c /= 2) {
+        const long long units = (long long)pl.gs_n_jb * ((m->n_r + c - 1) / c) * pl.gs_n_mg;
         if (units >= 2LL * m->num_sms) {
-            pl.gs_NS = ns;
+            ns = c;
             break;
         }
     }
-    pl.gs_n_sg = (m->n_r + pl.gs_NS - 1) / pl.gs_NS;
-    pl.gs_units = pl.gs_n_jb * pl.gs_n_sg * pl.gs_n_mg;
-    pl.gs_ns_s = 4;
-    while (pl.gs_ns_s > 2 && gsynth_tc_smem(pl) > (size_t)kSmemLimit) --pl.gs_ns_s;
-    if (gsynth_tc_smem(pl) > (size_t)kSmemLimit) return false;
+    size_t cb32 = 0;
+    if (!gsynth_plan_ns(m, 32, cb_off, cb32)) return false;
+    if (!gsynth_plan_ns(m, ns, cb_off, cb_bytes)) return false;
+    cb_bytes = std::max(cb_bytes, cb32);
     gs_off.assign(L + 1, 0);
-    cb_off.assign(L + 1, 0);
-    gs_bytes = cb_bytes = 0;
+    gs_bytes = 0;
     for (int mm = 1; mm <= L; ++mm) {
         const int n_kcm = (L + 1 - mm + 31) / 32;
         gs_off[mm] = gs_bytes;
         gs_bytes += (size_t)pl.gs_n_jb * n_kcm * 3 * gsc::T_TERM_BYTES;
-        cb_off[mm] = cb_bytes;
-        cb_bytes += (size_t)pl.gs_n_sg * n_kcm * pl.a_terms * 2 * pl.gs_NS * 64;
     }
     pl.th_smem = (int)theta_tc_smem(pl);
     pl.gs_smem = (int)gsynth_tc_smem(pl);
@@ -800,13 +835,19 @@ cudaError_t launch_theta_tc(mp_mesh *m)
     prm.stage_bytes = (uint32_t)(thc::F_BYTES + prm.bterms * pl.th_Nmax * 64);
     prm.scale = kFourPi * m->G;
     // the m = 0 column first (CUDA cores), then the orders m >= 1
+    cudaEvent_t ev;
+    prof_begin(m, "split_theta_contract_m0", &ev);
     cudaError_t e = launch_pdl(k_theta_m0, dim3((m->n_r + kM0Shells - 1) / kM0Shells, (m->L + kM0Deg) / kM0Deg),
                                dim3(256), 0, m->stream, prm);
+    prof_end(m, "split_theta_contract_m0", ev);
     if (e != cudaSuccess) return e;
     const int grid = std::min(pl.th_units, m->num_sms);
-    if (pl.a_terms == 2)
-        return launch_pdl(k_theta_tc<2, 3>, dim3(grid), dim3(thc::THREADS), pl.th_smem, m->stream, m->tm_F, prm);
-    return launch_pdl(k_theta_tc<3, 6>, dim3(grid), dim3(thc::THREADS), pl.th_smem, m->stream, m->tm_F, prm);
+    prof_begin(m, "split_theta_contract_tc", &ev);
+    e = pl.a_terms == 2
+            ? launch_pdl(k_theta_tc<2, 3>, dim3(grid), dim3(thc::THREADS), pl.th_smem, m->stream, m->tm_F, prm)
+            : launch_pdl(k_theta_tc<3, 6>, dim3(grid), dim3(thc::THREADS), pl.th_smem, m->stream, m->tm_F, prm);
+    prof_end(m, "split_theta_contract_tc", ev);
+    return e;
 }
 
 cudaError_t launch_gsynth_tc(mp_mesh *m)
@@ -835,13 +876,18 @@ cudaError_t launch_gsynth_tc(mp_mesh *m)
     const int n_jb = (m->n_t + 127) / 128;
     const int SB = (long long)n_jb * ((m->n_r + 31) / 32) >= 2LL * m->num_sms ? 32 : 8;
     const size_t smem0 = ((size_t)(m->L + 1) * 128 + (size_t)SB * (m->L + 1)) * sizeof(float2);
+    cudaEvent_t ev;
+    prof_begin(m, "split_theta_synth_m0", &ev);
     cudaError_t e = launch_pdl(k_gsynth_m0, dim3(n_jb, (m->n_r + SB - 1) / SB), dim3(256), smem0, m->stream,
                                (const float2 *)m->d_C0, (const float2 *)m->d_Itc0, m->d_G0, m->n_r, m->n_t, m->L, SB);
+    prof_end(m, "split_theta_synth_m0", ev);
     if (e != cudaSuccess) return e;
     const int grid = std::min(pl.gs_units, m->num_sms);
-    if (pl.a_terms == 2)
-        return launch_pdl(k_gsynth_tc<2, 3>, dim3(grid), dim3(gsc::THREADS), pl.gs_smem, m->stream, prm);
-    return launch_pdl(k_gsynth_tc<3, 6>, dim3(grid), dim3(gsc::THREADS), pl.gs_smem, m->stream, prm);
+    prof_begin(m, "split_theta_synth_tc", &ev);
+    e = pl.a_terms == 2 ? launch_pdl(k_gsynth_tc<2, 3>, dim3(grid), dim3(gsc::THREADS), pl.gs_smem, m->stream, prm)
+                        : launch_pdl(k_gsynth_tc<3, 6>, dim3(grid), dim3(gsc::THREADS), pl.gs_smem, m->stream, prm);
+    prof_end(m, "split_theta_synth_tc", ev);
+    return e;
 }
 
 }  // namespace mp

@@ -252,7 +252,8 @@ class Mesh:
 
     def moments_noalloc(self, rho, out):
         """Angular moments of rho into out [n_r * K_L] without device allocation
-        (mp_moments_noalloc; for callers that cannot allocate at the point of use)."""
+        (mp_moments_noalloc; for callers that cannot allocate at the point of use, such as
+        loops with a fixed memory budget or plug-ins whose host owns every allocation)."""
         _check(self._lib.mp_moments_noalloc(self._h, ctypes.c_void_p(_tensor_ptr(rho, self.cells, "rho")),
                                             ctypes.c_void_p(_tensor_ptr(out, self.shape[0] * self.n_moments,
                                                                         "out"))),

@@ -204,7 +204,8 @@ def test_profile_names_every_kernel(engine):
         for _ in range(3):
             mesh.solve()
         prof = mesh.profile_read()
-    theta = {"tensor": ("split_theta_contract_tc", "split_theta_synth_tc"),
+    theta = {"tensor": ("split_theta_contract_m0", "split_theta_contract_tc", "split_theta_synth_m0",
+                        "split_theta_synth_tc"),
              "cuda": ("split_theta_contract", "split_theta_synth")}[engine]
     assert set(prof) == {"split_phi_project_tc", "radial_scan", "split_synth_tc", *theta}
     assert all(v["launches"] == 3 and v["total_ms"] > 0 for v in prof.values())
