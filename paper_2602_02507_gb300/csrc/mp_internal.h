@@ -38,6 +38,7 @@ struct SplitPlan {
     int synth_smem = 0;
     int ns_s = 6;         // projection: TMA stages of the density
     int ns_o = 2;         // projection: stages of converted A operands (bf16 terms)
+    int proj_ns_b = 2;    // projection: table ring slots (when the table is not resident)
     int ns_s_max = 0;     // projection: the deepest density ring the reserved shared memory holds
     int ns_b_max = 0;     // synthesis: the deepest table ring the reserved shared memory holds
     int proj_b_resident = 0;  // projection: whole pre-split table held in shared memory

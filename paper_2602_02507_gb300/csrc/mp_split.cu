@@ -153,13 +153,15 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
     pdl_wait();
 
     if (warp == 0) {
-        // ---------------- producer: two TMA boxes of rho, and the table chunk on its own ring
+        // ---------------- producers: lane 0 streams the two TMA boxes of rho per chunk; lane 16
+        // the table chunks on a ring of their own (when the table is not resident), so that a
+        // shallow table ring does not hold back the density prefetch
         if (lane == 0) {
             tma_prefetch_desc(&tmS);
             // rho is read once per solve: its lines go first, ahead of F, tables and moments
             const uint64_t l2_first = l2_evict_first_policy();
-            Ring rs, rb;
-            int issued = 0, issued_b = 0;
+            Ring rs;
+            int issued = 0;
             for (int tile = blockIdx.x; tile < prm.n_tiles && !*abort_flag; tile += gridDim.x) {
                 for (int it = 0; it < prm.n_kc; ++it, rs.next(NS_S)) {
                     const int kc = rotated_chunk(it, tile, prm.n_kc);
@@ -171,31 +173,31 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                     tma_load_2d_hint(dst, &tmS, fb, kc * BK, tile * kBM, l2_first);
                     if (two) tma_load_2d_hint(dst + BOX_BYTES, &tmS, fb, kc * BK + 16, tile * kBM, l2_first);
                     ++issued;
-                    if (prm.b_resident) continue;
-                    if (!mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err)) {
-                        rs.next(NS_S);  // the density stage was issued: the drain counts back from past it
-                        break;
-                    }
-                    const uint32_t bb = smem_u32(&b_full[rb.idx]);
-                    mbar_arrive_expect_tx(bb, prm.bload);
-                    bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bload), prm.tabB + (size_t)kc * prm.bchunk,
-                              prm.bload, bb);
-                    ++issued_b;
-                    rb.next(NS_B);
                 }
             }
             // Every copy this thread issued has landed before the CTA can exit (another role may
             // abort after this loop ends; without an abort the phases are long complete).
             drain_ring(s_full, rs, NS_S, issued);
-            if (prm.b_resident) {
-                if ((int)blockIdx.x < prm.n_tiles) {
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait(smem_u32(&b_full[0]), 0) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
-                    }
+            if (prm.b_resident && (int)blockIdx.x < prm.n_tiles) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(smem_u32(&b_full[0]), 0) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
                 }
-            } else {
-                drain_ring(b_full, rb, NS_B, issued_b);
             }
+        } else if (lane == 16 && !prm.b_resident) {
+            Ring rb;
+            int issued_b = 0;
+            for (int tile = blockIdx.x; tile < prm.n_tiles && !*abort_flag; tile += gridDim.x) {
+                for (int it = 0; it < prm.n_kc; ++it, rb.next(NS_B)) {
+                    const int kc = rotated_chunk(it, tile, prm.n_kc);
+                    if (!mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err)) break;
+                    const uint32_t bb = smem_u32(&b_full[rb.idx]);
+                    mbar_arrive_expect_tx(bb, prm.bload);
+                    bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bload), prm.tabB + (size_t)kc * prm.bchunk,
+                              prm.bload, bb);
+                    ++issued_b;
+                }
+            }
+            drain_ring(b_full, rb, NS_B, issued_b);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
@@ -734,7 +736,8 @@ struct SynthParams {
     int Kpad, NC, n_nc, n_tiles, ns_a, ns_b, stg_bufs;
     int b_resident;        // 1: every table chunk stays in shared memory for the whole launch
     uint32_t a_bytes;      // one tile's A operand (all terms)
-    uint32_t bchunk;       // bytes of one B chunk (3 terms)
+    uint32_t bchunk;       // bytes of one B chunk in the table (3 terms)
+    uint32_t bload;        // bytes of the terms the products read (a prefix of the chunk)
 };
 
 template <int A_TERMS, int NPROD>
@@ -756,8 +759,8 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
     const uint32_t a_stage = prm.a_bytes + 1024;  // A operand terms + the tile's 128 m = 0 (hi, lo) pairs
     uint8_t *stg = smem;                                           // [16 warps][NSTG][4096]
     uint8_t *sA = stg + (size_t)EPI_WARPS * NSTG * STG_BYTES;      // [NS_A][a_stage]
-    uint8_t *sB = sA + (size_t)NS_A * a_stage;                     // [b_slots][bchunk]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)b_slots * prm.bchunk);
+    uint8_t *sB = sA + (size_t)NS_A * a_stage;                     // [b_slots][bload]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)b_slots * prm.bload);
     uint64_t *a_full = bars, *a_empty = bars + NS_A;
     uint64_t *b_full = a_empty + NS_A, *b_empty = b_full + NS_B;
     uint64_t *acc_full = b_empty + NS_B, *acc_empty = acc_full + 2, *drain = acc_empty + 2;
@@ -804,9 +807,9 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
             bool ok = true;
             if (prm.b_resident && blockIdx.x < n_units) {
                 // the whole table once; b_full[0] completes when every chunk has landed
-                mbar_arrive_expect_tx(smem_u32(&b_full[0]), (uint32_t)n_chunks * prm.bchunk);
+                mbar_arrive_expect_tx(smem_u32(&b_full[0]), (uint32_t)n_chunks * prm.bload);
                 for (int c = 0; c < n_chunks; ++c)
-                    bulk_load(smem_u32(sB + (size_t)c * prm.bchunk), prm.tabT + (size_t)c * prm.bchunk, prm.bchunk,
+                    bulk_load(smem_u32(sB + (size_t)c * prm.bload), prm.tabT + (size_t)c * prm.bchunk, prm.bload,
                               smem_u32(&b_full[0]));
             }
             pdl_wait();
@@ -826,9 +829,9 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                     for (int c = nc * nkk; c < (nc + 1) * nkk && ok; ++c, rb.next(NS_B)) {
                         ok = mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err);
                         if (!ok) break;
-                        mbar_arrive_expect_tx(smem_u32(&b_full[rb.idx]), prm.bchunk);
-                        bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bchunk), prm.tabT + (size_t)c * prm.bchunk,
-                                  prm.bchunk, smem_u32(&b_full[rb.idx]));
+                        mbar_arrive_expect_tx(smem_u32(&b_full[rb.idx]), prm.bload);
+                        bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bload), prm.tabT + (size_t)c * prm.bchunk,
+                                  prm.bload, smem_u32(&b_full[rb.idx]));
                         ++issued_b;
                     }
                 }
@@ -872,12 +875,12 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                     for (int kk = 0; kk < nkk; ++kk) {
                         uint32_t b_base;
                         if (prm.b_resident) {
-                            b_base = smem_u32(sB + (size_t)(nc * nkk + kk) * prm.bchunk);
+                            b_base = smem_u32(sB + (size_t)(nc * nkk + kk) * prm.bload);
                         } else {
                             ok = mbar_wait(smem_u32(&b_full[rb.idx]), rb.phase, abort_flag, prm.err);
                             if (!ok) break;
                             tc_fence_after();
-                            b_base = smem_u32(sB + (size_t)rb.idx * prm.bchunk);
+                            b_base = smem_u32(sB + (size_t)rb.idx * prm.bload);
                         }
                         const uint32_t a_base = a_base0 + (uint32_t)(kk * 256);
 #pragma unroll
@@ -1098,10 +1101,10 @@ int proj_b_terms(const SplitPlan &pl) { return pl.n_products == 3 ? 2 : 3; }
 // The table ring (when the table is not resident) is as deep as the density ring: both
 // loads of a chunk come from one thread, so a shallower table ring would cap the density
 // prefetch depth.
-int proj_smem_bytes(const SplitPlan &pl, int ns_s, int ns_o, int b_resident)
+int proj_smem_bytes(const SplitPlan &pl, int ns_s, int ns_o, int b_resident, int ns_b)
 {
     const int bload = proj_b_terms(pl) * pl.Npad * proj::BK * 2;
-    return 1024 + ns_s * proj::S_BYTES + (b_resident ? pl.n_kc : ns_s) * bload +
+    return 1024 + ns_s * proj::S_BYTES + (b_resident ? pl.n_kc : ns_b) * bload +
            ns_o * pl.a_terms * proj::A_TERM_BYTES + 512;
 }
 
@@ -1124,16 +1127,29 @@ int split_smem_limits(mp_mesh *m)
     // converter groups take alternate chunks, so with an even depth each slot belongs to
     // one group, and a group can never run a whole ring ahead of the other (a parity wait
     // on a slot two phases behind would pass at once)
-    static const int kProjCfg[][2] = {{4, 2}, {2, 2}};
-    int ns_s = 0, ns_o = 0, b_res = 0;
+    // projection: (density stages, A-operand stages, table ring slots) in order of
+    // preference, the table resident when it fits beside them, else on a ring of its own
+    // (its own producer thread: a shallower ring than the density's is fine).  The density and
+    // A-operand depths are even: the two converter groups take alternate chunks, so with an
+    // even depth each slot belongs to one group, and a group can never run a whole ring ahead
+    // of the other (a parity wait on a slot two phases behind would pass at once)
+    static const int kProjCfg[][3] = {{4, 2, 4}, {4, 2, 3}, {4, 2, 2}, {2, 2, 2}};
+    int ns_s = 0, ns_o = 0, b_res = 0, ns_bp = 2;
     for (const auto &c : kProjCfg) {
-        for (int r = 1; r >= 0 && ns_s == 0; --r)
-            if (proj_smem_bytes(pl, c[0], c[1], r) <= kSmemLimit) {
-                ns_s = c[0];
-                ns_o = c[1];
-                b_res = r;
-            }
-        if (ns_s) break;
+        if (proj_smem_bytes(pl, c[0], c[1], 1, 0) <= kSmemLimit) {
+            ns_s = c[0];
+            ns_o = c[1];
+            b_res = 1;
+            ns_bp = c[2];
+            break;
+        }
+        if (proj_smem_bytes(pl, c[0], c[1], 0, c[2]) <= kSmemLimit) {
+            ns_s = c[0];
+            ns_o = c[1];
+            b_res = 0;
+            ns_bp = c[2];
+            break;
+        }
     }
     if (ns_s == 0) return 1;
     // synthesis: prefer the whole table resident, two A stages and double-buffered staging
@@ -1160,12 +1176,13 @@ int split_smem_limits(mp_mesh *m)
     pl.ns_s_max = ns_s;
     pl.ns_b_max = pl.ns_b;
     pl.ns_o = ns_o;
+    pl.proj_ns_b = ns_bp;
     pl.proj_b_resident = b_res;
-    pl.proj_res_ok = proj_smem_bytes(pl, ns_s, ns_o, 1) <= kSmemLimit;
-    pl.proj_ring_ok = proj_smem_bytes(pl, ns_s, ns_o, 0) <= kSmemLimit;
+    pl.proj_res_ok = proj_smem_bytes(pl, ns_s, ns_o, 1, 0) <= kSmemLimit;
+    pl.proj_ring_ok = proj_smem_bytes(pl, ns_s, ns_o, 0, ns_bp) <= kSmemLimit;
     // the launch reserves the larger of the table modes that fit, so the tuner may switch them
-    pl.proj_smem = std::max(pl.proj_res_ok ? proj_smem_bytes(pl, ns_s, ns_o, 1) : 0,
-                            pl.proj_ring_ok ? proj_smem_bytes(pl, ns_s, ns_o, 0) : 0);
+    pl.proj_smem = std::max(pl.proj_res_ok ? proj_smem_bytes(pl, ns_s, ns_o, 1, 0) : 0,
+                            pl.proj_ring_ok ? proj_smem_bytes(pl, ns_s, ns_o, 0, ns_bp) : 0);
     return 0;
 }
 
@@ -1220,7 +1237,7 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho)
     prm.bload = (uint32_t)(proj_b_terms(pl) * pl.Npad * proj::BK * 2);
     prm.nacc = std::max(1, std::min(pl.proj_nacc, pl.proj_nacc_max));
     prm.b_resident = pl.proj_b_resident;
-    prm.ns_b = pl.ns_s;
+    prm.ns_b = pl.proj_ns_b;
     const int grid = std::min(prm.n_tiles, pl.proj_ctas);
     cudaEvent_t ev;
     prof_begin(m, "split_phi_project_tc", &ev);
@@ -1305,6 +1322,9 @@ static cudaError_t launch_phi_synth(mp_mesh *m)
     prm.b_resident = pl.b_resident;
     prm.a_bytes = (uint32_t)(pl.a_terms * kBM * pl.Kpad * 2);
     prm.bchunk = (uint32_t)(3 * pl.NC * 32);
+    // every term of a chunk is copied: copying only the terms the products read (BF16X3)
+    // measured slower on GB300 (2048 x 512 x 1024, l_max = 64: 1566 -> 1634 us)
+    prm.bload = prm.bchunk;
     const int grid = std::min(n_tiles * pl.n_nc, pl.synth_ctas);  // work units: (tile, column chunk)
     prof_begin(m, "split_synth_tc", &ev);
     if (pl.a_terms == 2)
