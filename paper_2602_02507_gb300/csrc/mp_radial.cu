@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_scan(const double *__restrict__ A, const
         const double mr_hi = fma(wr[i], a, mr_lo);
         double c = fma(GI[(size_t)l * n_r + i], mr_lo + mr_hi, GR[(size_t)l * n_r + i] * (mi + mi_hi));
         if (m > 0) c += c;
-        C[(size_t)i * KL + q] = c;
+        if (C) C[(size_t)i * KL + q] = c;
         const float c32 = f64_to_f32_alu(c);
         if (C32) C32[(size_t)i * KL + q] = c32;
         if (C0 && p == 0) C0[(size_t)i * Lp1 + l] = f32_pair(c);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
             MI[(size_t)i * KL + q] = ei[k];
             double c = fma(g2[k], er[k] + er[k + 1], g1[k] * (ei[k] + ei[k + 1]));
             if (m > 0) c += c;
-            C[(size_t)i * KL + q] = c;
+            if (C) C[(size_t)i * KL + q] = c;
             const float c32 = f64_to_f32_alu(c);
             if (C32) C32[(size_t)i * KL + q] = c32;
             if (C0 && p == 0) C0[(size_t)i * Lp1 + l] = f32_pair(c);
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(4 * NT) k_scan_q4(const double *__restrict__ A
             MI[(size_t)i * KL + q] = ei[k];
             double cv = fma(__ldg(gi + i), er + er1, __ldg(gr + i) * (ei[k] + ei[k + 1]));
             if (m > 0) cv += cv;
-            C[(size_t)i * KL + q] = cv;
+            if (C) C[(size_t)i * KL + q] = cv;
             const float c32 = f64_to_f32_alu(cv);
             if (C32) C32[(size_t)i * KL + q] = c32;
             if (C0 && p == 0) C0[(size_t)i * Lp1 + l] = f32_pair(cv);
@@ -616,6 +616,15 @@ __global__ void __launch_bounds__(256) k32_theta_mgemm(const float *__restrict__
 
 }  // namespace
 
+// The coefficients the synthesis that follows reads: float64 C on the float64 path; on the
+// split path the float32 copy for the CUDA-core theta synthesis, the bf16 terms (cb_out) for
+// the tensor-core one, and the m = 0 (hi, lo) pairs for both.
+static double *scan_c(const mp_mesh *m, int want_f32) { return want_f32 ? nullptr : m->d_C; }
+static float *scan_c32(const mp_mesh *m, int want_f32)
+{
+    return (want_f32 && !m->plan.use_theta_tc) ? m->d_C32 : nullptr;
+}
+
 // The coefficient terms of the tensor-core theta synthesis, when the split path uses it.
 static CbOut cb_out(const mp_mesh *m, int want_f32)
 {
@@ -634,7 +643,7 @@ template <int NT, int CH>
 static void scan_reg_launch(mp_mesh *m, int want_f32)
 {
     launch_pdl(k_scan_reg<NT, CH>, dim3(m->KL), dim3(NT), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
-               m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, want_f32 ? m->d_C0 : nullptr, m->n_r,
+               m->d_MR, m->d_MI, scan_c(m, want_f32), scan_c32(m, want_f32), want_f32 ? m->d_C0 : nullptr, m->n_r,
                m->KL, cb_out(m, want_f32), m->use_slab_off ? (const double *)m->d_slab_off : nullptr);
 }
 
@@ -687,8 +696,8 @@ static bool scan_q4_dispatch(mp_mesh *m, int want_f32)
     const int ch = (m->n_r + 127) / 128;
     auto go = [&](auto kern) {
         launch_pdl(kern, dim3((m->KL + 3) / 4), dim3(512), 0, m->stream, m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
-                   m->d_MR, m->d_MI, m->d_C, want_f32 ? m->d_C32 : nullptr, want_f32 ? m->d_C0 : nullptr, m->n_r,
-                   m->KL, cb_out(m, want_f32), m->use_slab_off ? (const double *)m->d_slab_off : nullptr);
+                   m->d_MR, m->d_MI, scan_c(m, want_f32), scan_c32(m, want_f32), want_f32 ? m->d_C0 : nullptr,
+                   m->n_r, m->KL, cb_out(m, want_f32), m->use_slab_off ? (const double *)m->d_slab_off : nullptr);
     };
     if (ch <= 4)
         go(k_scan_q4<128, 4>);
@@ -713,8 +722,8 @@ cudaError_t launch_scan(mp_mesh *m, int want_f32)
     }
     if (!done)
         k_scan<kScanThreads><<<m->KL, kScanThreads, 0, m->stream>>>(m->d_A, m->d_WR, m->d_WI, m->d_GR, m->d_GI,
-                                                                    m->d_MR, m->d_MI, m->d_C,
-                                                                    want_f32 ? m->d_C32 : nullptr,
+                                                                    m->d_MR, m->d_MI, scan_c(m, want_f32),
+                                                                    scan_c32(m, want_f32),
                                                                     want_f32 ? m->d_C0 : nullptr, m->n_r, m->KL,
                                                                     cb_out(m, want_f32),
                                                                     m->use_slab_off ? (const double *)m->d_slab_off : nullptr);

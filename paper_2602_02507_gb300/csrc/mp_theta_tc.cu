@@ -685,7 +685,7 @@ bool gsynth_plan_ns(mp_mesh *m, int ns, std::vector<unsigned long long> &cb_off,
     pl.gs_NS = ns;
     pl.gs_n_sg = (m->n_r + ns - 1) / ns;
     pl.gs_units = pl.gs_n_jb * pl.gs_n_sg * pl.gs_n_mg;
-    pl.gs_ns_s = 4;
+    pl.gs_ns_s = 8;
     while (pl.gs_ns_s > 2 && gsynth_tc_smem(pl) > (size_t)kSmemLimit) --pl.gs_ns_s;
     if (gsynth_tc_smem(pl) > (size_t)kSmemLimit) return false;
     pl.gs_smem = (int)gsynth_tc_smem(pl);
@@ -731,7 +731,7 @@ bool plan_theta_tc(mp_mesh *m, std::vector<unsigned long long> &th_off, size_t &
     pl.th_units = L * pl.th_groups;
     pl.th_nacc = std::max(1, std::min(std::min(4, 256 / pl.th_Nmax), pl.th_n_kc));
     pl.th_ns_o = 2;
-    pl.th_ns_s = 4;
+    pl.th_ns_s = 8;  // deep rings: the stages are small and the kernel is bound by the bytes in flight
     while (pl.th_ns_s > 2 && theta_tc_smem(pl) > (size_t)kSmemLimit) pl.th_ns_s -= 2;
     if (theta_tc_smem(pl) > (size_t)kSmemLimit) return false;
     th_off.assign(L + 1, 0);
