@@ -328,10 +328,11 @@ def lognormal(n_r=1024, n_theta=256, n_phi=512, L=32, seed=3, sigma=1.0, lmax_fi
     return Workload(Mesh(r, th, ph, L, G_CGS, "lognormal"), rho)
 
 
-def large(materialize=False) -> Workload:
+def large(materialize=False, n_r=2048) -> Workload:
     """2048 x 512 x 1024 cells, L = 64; returned as the separable factors
-    rho = profile[i] * angular[j, k] unless materialize is set (8.6 GB)."""
-    return presn(n_r=2048, n_theta=512, n_phi=1024, L=64, seed=4, amp=1e-2, lmax_pert=4,
+    rho = profile[i] * angular[j, k] unless materialize is set (8.6 GB).  A smaller n_r
+    keeps the angular grid, l_max and density recipe (profiling captures of its kernels)."""
+    return presn(n_r=n_r, n_theta=512, n_phi=1024, L=64, seed=4, amp=1e-2, lmax_pert=4,
                  amp_hi=1e-3, lmax_hi=64, materialize=materialize)
 
 
