@@ -189,7 +189,11 @@ __global__ void __launch_bounds__(thc::THREADS, 1) k_theta_tc(const __grid_const
     } else {
         // ---------------- converters (F -> bf16 terms) + epilogue (accumulators -> moments)
         const int cw = warp - 2, grp = cw / GROUP_WARPS, qd = warp & 3, half = (cw >> 2) & 1;
-        const int row = qd * 32 + lane;                 // A row: (a = row >> 6, shell = row & 63)
+        // this thread converts F row (a = row >> 6, shell row & 63) of the boxes and writes it
+        // to MMA row mrow = 2 shell + a, so that each shell's cos and sin accumulators sit in
+        // adjacent lanes and the epilogue's stores of a warp pair up in 16-byte pieces
+        const int row = qd * 32 + lane;
+        const int mrow = 2 * (row & 63) + (row >> 6);
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
         Ring rs, ro;
         if (grp) {
@@ -205,8 +209,8 @@ __global__ void __launch_bounds__(thc::THREADS, 1) k_theta_tc(const __grid_const
             tc_fence_after();
             const int m = 1 + eu / prm.n_groups, g = eu - (m - 1) * prm.n_groups;
             const int Nm = round16(prm.L + 1 - m);
-            const int i = g * SHELLS + (row & 63);
-            const int p = 2 * m - 1 + (row >> 6);
+            const int i = g * SHELLS + (row >> 1);  // accumulator lane row holds MMA row `row`
+            const int p = 2 * m - 1 + (row & 1);
             double *Ai = prm.A + (size_t)i * prm.KL + p;
             for (int cg = 2 * grp + half; cg * 8 < Nm; cg += 4) {
                 uint32_t v[4][8];
@@ -265,8 +269,8 @@ __global__ void __launch_bounds__(thc::THREADS, 1) k_theta_tc(const __grid_const
                         if (A_TERMS == 3) w2[2 * q + h] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
                     }
                 }
-                uint8_t *adst = sA + (size_t)oidx * A_TERMS * A_TERM_BYTES + (row >> 3) * SBO + half * 256 +
-                                (row & 7) * 16;
+                uint8_t *adst = sA + (size_t)oidx * A_TERMS * A_TERM_BYTES + (mrow >> 3) * SBO + half * 256 +
+                                (mrow & 7) * 16;
 #pragma unroll
                 for (int kg = 0; kg < 2; ++kg) {
                     *reinterpret_cast<uint4 *>(adst + kg * 128) =
