@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         }
         int par = 0;  // parity of the CTA-wide chunk sequence number
         float sref = 0.0f, sref_prev = 0.0f;
-        uint32_t efmax = 0;  // largest float64 exponent field seen (flags values beyond float32)
+        uint32_t efmax = 0;  // largest float64 exponent field seen by the checked conversion
+        uint32_t over = 0;   // fast conversion: bit 15 or 31 set once a magnitude reached 2^128
         bool ok = true;
 
         // the accumulator of a finished tile: F = D + sref colsum, stored per shell as rows of
@@ -336,27 +337,50 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                 const int kfirst = kc * BK + half * 16;           // first cell of this thread's box
                 const bool full = kfirst + 16 <= prm.n_p;         // warp-uniform
                 uint32_t w0[8], w1[8], w2[8];
-#pragma unroll
-                for (int cc = 0; cc < 8; ++cc) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((cc ^ (row & 7)) << 4));
-                    uint32_t e0, e1;
-                    float x0 = f64w_to_f32_fast(v.x, v.y, e0) - sref;
-                    float x1 = f64w_to_f32_fast(v.z, v.w, e1) - sref;
-                    if (!full) {
-                        // cells past the last azimuthal cell hold no data: zero deviation
-                        const bool in0 = kfirst + 2 * cc < prm.n_p, in1 = kfirst + 2 * cc + 1 < prm.n_p;
-                        x0 = in0 ? x0 : 0.0f;
-                        x1 = in1 ? x1 : 0.0f;
-                        e0 = in0 ? e0 : 0u;
-                        e1 = in1 ? e1 : 0u;
-                    }
-                    efmax = max(efmax, max(e0, e1));
+                // the deviations' bf16 terms of one pair of cells
+                auto split_pair = [&](int cc, float x0, float x1) {
                     const uint32_t t0 = pack_bf16x2(x0, x1);
                     const float r0 = x0 - bf16lo_to_f32(t0), r1 = x1 - bf16hi_to_f32(t0);
                     const uint32_t t1 = pack_bf16x2(r0, r1);
                     w0[cc] = t0;
                     w1[cc] = t1;
                     if (A_TERMS == 3) w2[cc] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
+                };
+                // Fast path (every magnitude in float32's normal range, the common case): the
+                // conversion without per-value selects.  Two SWAR subtractions per pair of
+                // values test the upper halves of their high words (exponent and four mantissa
+                // bits) against 2^-126 (0x3810) and 2^128 (0x47F0); a value below the first
+                // sends the chunk through the checked conversion again, one at or above the
+                // second (or an infinity or nan) is reported at the end.
+                uint32_t under = 0x80008000u;
+                if (full) {
+#pragma unroll
+                    for (int cc = 0; cc < 8; ++cc) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((cc ^ (row & 7)) << 4));
+                        const uint32_t hh = __byte_perm(v.y, v.w, 0x7632) | 0x80008000u;
+                        under &= hh - 0x38103810u;
+                        over |= hh - 0x47F047F0u;
+                        split_pair(cc, f64w_to_f32_inrange(v.x, v.y) - sref, f64w_to_f32_inrange(v.z, v.w) - sref);
+                    }
+                }
+                if (!full || (under & 0x80008000u) != 0x80008000u) {
+#pragma unroll
+                    for (int cc = 0; cc < 8; ++cc) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((cc ^ (row & 7)) << 4));
+                        uint32_t e0, e1;
+                        float x0 = f64w_to_f32_fast(v.x, v.y, e0) - sref;
+                        float x1 = f64w_to_f32_fast(v.z, v.w, e1) - sref;
+                        if (!full) {
+                            // cells past the last azimuthal cell hold no data: zero deviation
+                            const bool in0 = kfirst + 2 * cc < prm.n_p, in1 = kfirst + 2 * cc + 1 < prm.n_p;
+                            x0 = in0 ? x0 : 0.0f;
+                            x1 = in1 ? x1 : 0.0f;
+                            e0 = in0 ? e0 : 0u;
+                            e1 = in1 ? e1 : 0u;
+                        }
+                        efmax = max(efmax, max(e0, e1));
+                        split_pair(cc, x0, x1);
+                    }
                 }
                 // K groups 2 half and 2 half + 1 of the [128 x 32] A tile, each term
                 uint8_t *adst = sA + (size_t)oidx * A_TERMS * A_TERM_BYTES + (row >> 3) * SBO + half * 256 +
@@ -385,7 +409,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         }
         if (ok && prev_tile >= 0) epilogue(prev_tile, lt - 1, sref_prev);
         // exponent fields above float32's range (including inf / nan, 0x7FF) are reported
-        if (efmax > (1150u << 20)) atomicOr(prm.err, DEV_ERR_NONFINITE);
+        if (efmax > (1150u << 20) || (over & 0x80008000u)) atomicOr(prm.err, DEV_ERR_NONFINITE);
     }
 
     tc_fence_before();

@@ -367,6 +367,14 @@ __device__ __forceinline__ float f64w_to_f32_fast(uint32_t lo, uint32_t hi, uint
     return __uint_as_float(ef >= (897u << 20) ? r : sign);
 }
 
+// The same conversion for a magnitude known to lie in float32's normal range (no
+// range select): the caller checks the range on its own.
+__device__ __forceinline__ float f64w_to_f32_inrange(uint32_t lo, uint32_t hi)
+{
+    const uint32_t t = __funnelshift_l(lo, hi, 3);
+    return __uint_as_float((((t & 0x7FFFFFFFu) | (hi & 0x80000000u)) ^ 0x40000000u) | 1u);
+}
+
 // float64 -> float32 with integer ops (round to nearest, ties away from zero):
 // magnitudes below float32's normal range give signed zero, above it signed
 // infinity (so do inf and nan).
