@@ -34,6 +34,49 @@ def test_nonfinite_density_is_reported(prec):
         mesh.synchronize()  # the error word was cleared
 
 
+@pytest.mark.parametrize("value", [float("inf"), 1e39])
+def test_density_beyond_float32_is_reported_on_the_split_path(value):
+    """The split path converts the density to float32: a magnitude of 2^128 or more (or an
+    infinity) cannot be represented and is reported, whichever conversion path the chunk
+    takes (a zero in the same chunk sends it through the checked conversion)."""
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = W.presn(n_r=8, n_theta=16, n_phi=32, L=4)
+    m = w.mesh
+    for with_zero in (False, True):
+        rho = torch.from_numpy(w.rho).cuda()
+        rho.view(-1)[1234] = value
+        if with_zero:
+            rho.view(-1)[1235] = 0.0
+        with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3") as mesh:
+            mesh.set_density(rho)
+            mesh.solve()
+            with pytest.raises(mpl.MultipoleError) as ei:
+                mesh.synchronize()
+            assert ei.value.name == "MP_ERR_NONFINITE", with_zero
+
+
+@pytest.mark.parametrize("engine", ["tensor", "cuda"])
+def test_zero_and_tiny_densities_match_the_oracle(engine):
+    """Zeros and magnitudes below float32's normal range (which the split path takes as
+    zero) scattered through the density, and whole rows of them, against the oracle: the
+    projection's chunks that hold them go through its checked conversion."""
+    w = W.presn(n_r=16, n_theta=32, n_phi=64, L=6)
+    rng = np.random.default_rng(7)
+    flat = w.rho.reshape(-1)
+    idx = rng.choice(flat.size, size=flat.size // 50, replace=False)
+    flat[idx[: idx.size // 2]] = 0.0
+    flat[idx[idx.size // 2:]] = 1e-300
+    w.rho[3, 5, :] = 1e-45   # a whole row below float32's range
+    w.rho[4, 7, :] = 0.0     # a whole row of zeros
+    w.rho[5, 9, 17:] = 0.0   # a row that ends in zeros
+    ref = oracle_solve(w)["phi"]
+    phi = gpu_solve(w, "bf16x3", want_moments=False, engine=engine)["phi"]
+    err = phi_rel_err(phi, ref)
+    print(f"zeros and tiny values, {engine}: phi {err:.2e}")
+    assert err <= 1e-6
+
+
 @pytest.mark.parametrize("engine", ["tensor", "cuda"])
 @pytest.mark.parametrize("shape,L", [((8, 16, 32), 4), ((64, 32, 64), 8)])
 def test_expired_device_wait_reports_timeout_and_the_mesh_recovers(shape, L, engine):
