@@ -262,8 +262,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         }
         int par = 0;  // parity of the CTA-wide chunk sequence number
         float sref = 0.0f, sref_prev = 0.0f;
-        uint32_t efmax = 0;  // largest float64 exponent field seen by the checked conversion
-        uint32_t over = 0;   // fast conversion: bit 15 or 31 set once a magnitude reached 2^128
+        uint32_t efmax = 0;  // largest float64 exponent field seen (flags values beyond float32)
         bool ok = true;
 
         // the accumulator of a finished tile: F = D + sref colsum, stored per shell as rows of
@@ -337,33 +336,38 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                 const int kfirst = kc * BK + half * 16;           // first cell of this thread's box
                 const bool full = kfirst + 16 <= prm.n_p;         // warp-uniform
                 uint32_t w0[8], w1[8], w2[8];
-                // the deviations' bf16 terms of one pair of cells
-                auto split_pair = [&](int cc, float x0, float x1) {
-                    const uint32_t t0 = pack_bf16x2(x0, x1);
-                    const float r0 = x0 - bf16lo_to_f32(t0), r1 = x1 - bf16hi_to_f32(t0);
-                    const uint32_t t1 = pack_bf16x2(r0, r1);
+                // the deviations' bf16 terms of one pair of cells (packed float32 pairs)
+                auto split_pair = [&](int cc, float2 x) {
+                    const uint32_t t0 = pack_bf16x2(x.x, x.y);
+                    const float2 r = sub_f32x2(x, make_float2(bf16lo_to_f32(t0), bf16hi_to_f32(t0)));
+                    const uint32_t t1 = pack_bf16x2(r.x, r.y);
                     w0[cc] = t0;
                     w1[cc] = t1;
-                    if (A_TERMS == 3) w2[cc] = pack_bf16x2(r0 - bf16lo_to_f32(t1), r1 - bf16hi_to_f32(t1));
+                    if (A_TERMS == 3) {
+                        const float2 r2 = sub_f32x2(r, make_float2(bf16lo_to_f32(t1), bf16hi_to_f32(t1)));
+                        w2[cc] = pack_bf16x2(r2.x, r2.y);
+                    }
                 };
+                const float2 sref2 = make_float2(sref, sref);
                 // Fast path (every magnitude in float32's normal range, the common case): the
                 // conversion without per-value selects.  Two SWAR subtractions per pair of
                 // values test the upper halves of their high words (exponent and four mantissa
-                // bits) against 2^-126 (0x3810) and 2^128 (0x47F0); a value below the first
-                // sends the chunk through the checked conversion again, one at or above the
-                // second (or an infinity or nan) is reported at the end.
-                uint32_t under = 0x80008000u;
+                // bits) against 2^-126 (0x3810) and 2^128 (0x47F0); a value below the first, or
+                // at or above the second (an infinity or a nan too), sends the chunk through the
+                // checked conversion again, which zeroes the small ones and records the
+                // exponent of the large ones for the report at the end.
+                uint32_t bad = 0;  // bit 15 or 31: a magnitude outside [2^-126, 2^128)
                 if (full) {
 #pragma unroll
                     for (int cc = 0; cc < 8; ++cc) {
                         const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((cc ^ (row & 7)) << 4));
                         const uint32_t hh = __byte_perm(v.y, v.w, 0x7632) | 0x80008000u;
-                        under &= hh - 0x38103810u;
-                        over |= hh - 0x47F047F0u;
-                        split_pair(cc, f64w_to_f32_inrange(v.x, v.y) - sref, f64w_to_f32_inrange(v.z, v.w) - sref);
+                        bad |= ~(hh - 0x38103810u) | (hh - 0x47F047F0u);
+                        split_pair(cc, sub_f32x2(make_float2(f64w_to_f32_inrange(v.x, v.y),
+                                                             f64w_to_f32_inrange(v.z, v.w)), sref2));
                     }
                 }
-                if (!full || (under & 0x80008000u) != 0x80008000u) {
+                if (!full || (bad & 0x80008000u)) {
 #pragma unroll
                     for (int cc = 0; cc < 8; ++cc) {
                         const uint4 v = *reinterpret_cast<const uint4 *>(srow + ((cc ^ (row & 7)) << 4));
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                             e1 = in1 ? e1 : 0u;
                         }
                         efmax = max(efmax, max(e0, e1));
-                        split_pair(cc, x0, x1);
+                        split_pair(cc, make_float2(x0, x1));
                     }
                 }
                 // K groups 2 half and 2 half + 1 of the [128 x 32] A tile, each term
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         }
         if (ok && prev_tile >= 0) epilogue(prev_tile, lt - 1, sref_prev);
         // exponent fields above float32's range (including inf / nan, 0x7FF) are reported
-        if (efmax > (1150u << 20) || (over & 0x80008000u)) atomicOr(prm.err, DEV_ERR_NONFINITE);
+        if (efmax > (1150u << 20)) atomicOr(prm.err, DEV_ERR_NONFINITE);
     }
 
     tc_fence_before();

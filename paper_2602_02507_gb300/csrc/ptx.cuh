@@ -434,6 +434,18 @@ __device__ __forceinline__ float2 f32_pair(double x)
     return make_float2(hi, f64_to_f32_alu(x - f32_to_f64_alu(hi)));
 }
 
+// Two float32 subtractions in one packed instruction (each rounded to nearest, as the
+// scalar form): a - b for both halves.
+__device__ __forceinline__ float2 sub_f32x2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rr;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rr, ra, rb;\n\tmov.b64 {%0, %1}, rr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 // Round-to-nearest bf16 pair packed in one word (x in the low half).
 __device__ __forceinline__ uint32_t pack_bf16x2(float x, float y)
 {
