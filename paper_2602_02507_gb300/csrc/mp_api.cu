@@ -108,8 +108,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// [rows][cols] float64, 128-byte swizzled boxes of [box_rows][16].
-static mp_status make_map(CUtensorMap *map, const void *ptr, long long rows, int cols, int box_rows)
+// [rows][cols] float64 in boxes of [box_rows][box_cols]: 16 columns with a 128-byte swizzle,
+// 8 with a 64-byte one.
+static mp_status make_map(CUtensorMap *map, const void *ptr, long long rows, int cols, int box_rows,
+                          int box_cols = 16)
 {
     auto fn = encode_fn();
     if (!fn) return set_error(MP_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -117,11 +119,12 @@ static mp_status make_map(CUtensorMap *map, const void *ptr, long long rows, int
         return set_error(MP_ERR_INVALID_ARG, "split precision needs 16-byte aligned density/potential buffers");
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(double)};
-    cuuint32_t box[2] = {16u, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1u, 1u};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(ptr), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    box_cols == 16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(MP_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return MP_OK;
 }
@@ -244,7 +247,7 @@ static mp_status run_potential(mp_mesh *m, double *phi)
         MP_TRY(launch_fp64_synth(m, phi));
     } else {
         if (m->tm_phi_ptr != phi) {
-            mp_status st = make_map(&m->tm_phi, phi, m->R, m->n_p, 32);
+            mp_status st = make_map(&m->tm_phi, phi, m->R, m->n_p, 32, m->plan.stg_cols);
             if (st != MP_OK) return st;
             m->tm_phi_ptr = phi;
         }

@@ -47,6 +47,7 @@ struct SplitPlan {
     int ns_a = 2;         // synthesis: A-operand stages
     int b_resident = 0;   // synthesis: whole table held in shared memory
     int stg_bufs = 2;     // synthesis: TMA store staging boxes per epilogue warp
+    int stg_cols = 16;    // synthesis: float64 columns of a staging box (16: 128B swizzle, 8: 64B)
     int proj_nacc = 1;    // projection: accumulators per tile (K chunks dealt round-robin)
     int proj_nacc_max = 1;
     int scan_threads = 128;  // radial recurrences: threads (shell chunks) per moment column

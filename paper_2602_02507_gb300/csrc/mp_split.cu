@@ -750,7 +750,8 @@ __global__ void __launch_bounds__(256) k_gsynth_mgemm(const float *__restrict__ 
 // write Phi with TMA stores.
 // ----------------------------------------------------------------------------
 namespace synth {
-constexpr int STG_BYTES = 32 * 16 * 8;  // TMA store box [32 rows][16 float64], 128B swizzle
+// TMA store boxes of [32 rows][16 float64] (128B swizzle) or [32 rows][8 float64] (64B swizzle)
+__host__ __device__ constexpr int stg_bytes(int cols) { return 32 * cols * 8; }
 constexpr int EPI_WARPS = 16;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 }
@@ -761,7 +762,7 @@ struct SynthParams {
     const uint8_t *tabT;   // [n_nc][Kpad/16][3][NC x 16] bf16, canonical layout
     int *err;
     long long R;
-    int Kpad, NC, n_nc, n_tiles, ns_a, ns_b, stg_bufs;
+    int Kpad, NC, n_nc, n_tiles, ns_a, ns_b, stg_bufs, stg_cols;
     int b_resident;        // 1: every table chunk stays in shared memory for the whole launch
     uint32_t a_bytes;      // one tile's A operand (all terms)
     uint32_t bchunk;       // bytes of one B chunk in the table (3 terms)
@@ -775,7 +776,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
     using namespace synth;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int NS_A = prm.ns_a, NS_B = prm.ns_b, NSTG = prm.stg_bufs;
+    const int NS_A = prm.ns_a, NS_B = prm.ns_b, NSTG = prm.stg_bufs, STG_BYTES = stg_bytes(prm.stg_cols);
     const int Kpad = prm.Kpad, NC = prm.NC;
     const int nkk = Kpad / 16;
     const int n_chunks = prm.n_nc * nkk;
@@ -785,7 +786,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
     const int n_units = prm.n_tiles * prm.n_nc;
     const int b_slots = prm.b_resident ? n_chunks : NS_B;
     const uint32_t a_stage = prm.a_bytes + 1024;  // A operand terms + the tile's 128 m = 0 (hi, lo) pairs
-    uint8_t *stg = smem;                                           // [16 warps][NSTG][4096]
+    uint8_t *stg = smem;                                           // [16 warps][NSTG][STG_BYTES]
     uint8_t *sA = stg + (size_t)EPI_WARPS * NSTG * STG_BYTES;      // [NS_A][a_stage]
     uint8_t *sB = sA + (size_t)NS_A * a_stage;                     // [b_slots][bload]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)b_slots * prm.bload);
@@ -971,29 +972,59 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                     uint32_t v[16];
                     tmem_ld16(tcol + (uint32_t)(ch * 16), v);
                     tmem_ld_wait();
-                    uint8_t *st = stg + (size_t)(cw * NSTG + cs) * STG_BYTES;
-                    if (++cs == NSTG) cs = 0;
-                    if (lane == 0) {
-                        if (NSTG > 1)
-                            bulk_wait_read_le1();
-                        else
-                            bulk_wait_read_all();
-                    }
-                    __syncwarp();
-                    uint8_t *srow = st + lane * 128;
+                    // one box of 16 columns or two of 8: with two or more staging boxes a warp
+                    // fills one while the bulk-copy engine still reads another.  Phi = m >= 1 part
+                    // + m = 0 column (low part first: one rounding of the sum).
+                    auto next_box = [&]() -> uint8_t * {
+                        uint8_t *st = stg + (size_t)(cw * NSTG + cs) * STG_BYTES;
+                        if (++cs == NSTG) cs = 0;
+                        if (lane == 0) {  // this box's last store has read it
+                            if (NSTG >= 4)
+                                bulk_wait_read_le3();
+                            else if (NSTG > 1)
+                                bulk_wait_read_le1();
+                            else
+                                bulk_wait_read_all();
+                        }
+                        __syncwarp();
+                        return st;
+                    };
+                    auto store_box = [&](uint8_t *st, int col) {
+                        fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0 && box_valid) {
+                            tma_store_2d_hint(&tmPhi, smem_u32(st), col, (int)box_row, l2_first);
+                            bulk_commit();
+                        }
+                    };
+                    if (prm.stg_cols == 16) {
+                        // 128-byte swizzle: 16-byte piece e of row `lane` sits at e ^ (lane & 7)
+                        uint8_t *st = next_box();
+                        uint8_t *srow = st + lane * 128;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        uint32_t lo0, hi0, lo1, hi1;
-                        // Phi = m >= 1 part + m = 0 column (low part first: one rounding of the sum)
-                        f32_to_f64w_finite((__uint_as_float(v[2 * e]) + g0.y) + g0.x, lo0, hi0);
-                        f32_to_f64w_finite((__uint_as_float(v[2 * e + 1]) + g0.y) + g0.x, lo1, hi1);
-                        *reinterpret_cast<uint4 *>(srow + ((e ^ (lane & 7)) << 4)) = make_uint4(lo0, hi0, lo1, hi1);
-                    }
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0 && box_valid) {
-                        tma_store_2d_hint(&tmPhi, smem_u32(st), nc * NC + ch * 16, (int)box_row, l2_first);
-                        bulk_commit();
+                        for (int e = 0; e < 8; ++e) {
+                            uint32_t lo0, hi0, lo1, hi1;
+                            f32_to_f64w_finite((__uint_as_float(v[2 * e]) + g0.y) + g0.x, lo0, hi0);
+                            f32_to_f64w_finite((__uint_as_float(v[2 * e + 1]) + g0.y) + g0.x, lo1, hi1);
+                            *reinterpret_cast<uint4 *>(srow + ((e ^ (lane & 7)) << 4)) = make_uint4(lo0, hi0, lo1, hi1);
+                        }
+                        store_box(st, nc * NC + ch * 16);
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            // 64-byte swizzle: 16-byte piece e of row `lane` sits at e ^ ((lane >> 1) & 3)
+                            uint8_t *st = next_box();
+                            uint8_t *srow = st + lane * 64;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                uint32_t lo0, hi0, lo1, hi1;
+                                f32_to_f64w_finite((__uint_as_float(v[8 * h + 2 * e]) + g0.y) + g0.x, lo0, hi0);
+                                f32_to_f64w_finite((__uint_as_float(v[8 * h + 2 * e + 1]) + g0.y) + g0.x, lo1, hi1);
+                                *reinterpret_cast<uint4 *>(srow + ((e ^ ((lane >> 1) & 3)) << 4)) =
+                                    make_uint4(lo0, hi0, lo1, hi1);
+                            }
+                            store_box(st, nc * NC + ch * 16 + 8 * h);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -1136,11 +1167,11 @@ int proj_smem_bytes(const SplitPlan &pl, int ns_s, int ns_o, int b_resident, int
            ns_o * pl.a_terms * proj::A_TERM_BYTES + 512;
 }
 
-int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs)
+int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs, int stg_cols)
 {
     const int bchunk = 3 * pl.NC * 32;
     const int a_stage = pl.a_terms * kBM * pl.Kpad * 2 + 1024;
-    return 1024 + synth::EPI_WARPS * stg_bufs * synth::STG_BYTES + ns_a * a_stage + b_slots * bchunk + 512;
+    return 1024 + synth::EPI_WARPS * stg_bufs * synth::stg_bytes(stg_cols) + ns_a * a_stage + b_slots * bchunk + 512;
 }
 
 
@@ -1150,11 +1181,6 @@ int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs)
 int split_smem_limits(mp_mesh *m)
 {
     SplitPlan &pl = m->plan;
-    // projection: (density stages, A-operand stages) in order of preference, the table
-    // resident when it fits beside them, else a ring.  Both depths are even: the two
-    // converter groups take alternate chunks, so with an even depth each slot belongs to
-    // one group, and a group can never run a whole ring ahead of the other (a parity wait
-    // on a slot two phases behind would pass at once)
     // projection: (density stages, A-operand stages, table ring slots) in order of
     // preference, the table resident when it fits beside them, else on a ring of its own
     // (its own producer thread: a shallower ring than the density's is fine).  The density and
@@ -1180,21 +1206,30 @@ int split_smem_limits(mp_mesh *m)
         }
     }
     if (ns_s == 0) return 1;
-    // synthesis: prefer the whole table resident, two A stages and double-buffered staging
+    // synthesis: 8 KB of staging per epilogue warp (two boxes of 16 columns), then double-buffered
+    // 4 KB (two boxes of 8 columns), then a single box; within each, the whole table resident and
+    // two A stages first.  Measured on GB300: a log-normal 1024 x 256 x 512, l_max = 32 mesh ran
+    // it in 176 us with one A stage beside two 16-column boxes, 189 us with four 8-column ones
+    // and 207 us with two A stages and a three-slot table ring beside two 8-column ones; the
+    // 2048 x 512 x 1024, l_max = 64 mesh, where only 4 KB fit, in 1551 us with two 8-column boxes
+    // against 1565 us with one 16-column box.
     const int n_chunks = pl.n_nc * (pl.Kpad / 16);
     struct Cfg {
-        int ns_a, resident, ns_b, stg;
+        int ns_a, resident, ns_b, stg, cols;
     };
-    const Cfg cfgs[] = {{2, 1, 0, 2}, {2, 0, 3, 2}, {2, 0, 2, 2}, {1, 0, 2, 2}, {2, 0, 2, 1}, {1, 0, 2, 1}};
+    const Cfg cfgs[] = {{2, 1, 0, 2, 16}, {2, 0, 3, 2, 16}, {2, 0, 2, 2, 16}, {1, 0, 2, 2, 16},
+                        {2, 1, 0, 2, 8},  {2, 0, 3, 2, 8},  {2, 0, 2, 2, 8},  {1, 0, 2, 2, 8},
+                        {2, 0, 2, 1, 16}, {1, 0, 2, 1, 16}};
     bool found = false;
     for (const Cfg &c : cfgs) {
         const int b_slots = c.resident ? n_chunks : c.ns_b;
-        if (synth_smem_bytes(pl, c.ns_a, b_slots, c.stg) <= kSmemLimit) {
+        if (synth_smem_bytes(pl, c.ns_a, b_slots, c.stg, c.cols) <= kSmemLimit) {
             pl.ns_a = c.ns_a;
             pl.b_resident = c.resident;
             pl.ns_b = c.resident ? 1 : c.ns_b;
             pl.stg_bufs = c.stg;
-            pl.synth_smem = synth_smem_bytes(pl, c.ns_a, b_slots, c.stg);
+            pl.stg_cols = c.cols;
+            pl.synth_smem = synth_smem_bytes(pl, c.ns_a, b_slots, c.stg, c.cols);
             found = true;
             break;
         }
@@ -1347,6 +1382,7 @@ static cudaError_t launch_phi_synth(mp_mesh *m)
     prm.ns_a = pl.ns_a;
     prm.ns_b = pl.ns_b;
     prm.stg_bufs = pl.stg_bufs;
+    prm.stg_cols = pl.stg_cols;
     prm.b_resident = pl.b_resident;
     prm.a_bytes = (uint32_t)(pl.a_terms * kBM * pl.Kpad * 2);
     prm.bchunk = (uint32_t)(3 * pl.NC * 32);
