@@ -1104,15 +1104,17 @@ static std::string tune_key(const mp_mesh *m)
 
 }  // extern "C"
 
-// One point of the tuner's search space.
+// One point of the tuner's search space: density ring depth, synthesis stage configuration
+// (synth_cfg_apply), threads per moment column of the recurrences, projection table
+// residency, theta engine, theta synthesis shells per unit, projection accumulators.
 struct TuneCfg {
-    int ns_s, ns_b, sw, br, tc, gs_ns, nacc;
+    int ns_s, sy, sw, br, tc, gs_ns, nacc;
 };
 
 static TuneCfg current_cfg(const mp_mesh *m)
 {
     const SplitPlan &p = m->plan;
-    return {p.ns_s, p.ns_b, p.scan_threads, p.proj_b_resident, p.use_theta_tc, p.gs_NS, p.proj_nacc};
+    return {p.ns_s, p.synth_cfg, p.scan_threads, p.proj_b_resident, p.use_theta_tc, p.gs_NS, p.proj_nacc};
 }
 
 // Whether a configuration (a cache line, or a tuner candidate) fits this mesh's plan.
@@ -1122,7 +1124,7 @@ static bool cfg_fits(const mp_mesh *m, const TuneCfg &c)
     if (!(c.sw == 64 || c.sw == 128 || c.sw == 256)) return false;
     if (m->eff_prec == MP_PREC_FP64) return true;
     // the density ring is even (the two converter groups alternate over its slots)
-    return c.ns_s >= 2 && !(c.ns_s & 1) && c.ns_s <= p.ns_s_max && c.ns_b >= 1 && c.ns_b <= p.ns_b_max &&
+    return c.ns_s >= 2 && !(c.ns_s & 1) && c.ns_s <= p.ns_s_max && synth_cfg_fits(p, c.sy) &&
            (c.br ? p.proj_res_ok : p.proj_ring_ok) && (c.tc == 0 || p.theta_tc_ok) &&
            (c.gs_ns == 8 || c.gs_ns == 16 || c.gs_ns == 32) && c.nacc >= 1 && c.nacc <= p.proj_nacc_max;
 }
@@ -1131,7 +1133,11 @@ static mp_status apply_cfg(mp_mesh *m, const TuneCfg &c)
 {
     SplitPlan &p = m->plan;
     p.ns_s = c.ns_s;
-    p.ns_b = c.ns_b;
+    if (m->eff_prec != MP_PREC_FP64) {
+        const int cols = p.stg_cols;
+        synth_cfg_apply(p, c.sy);
+        if (p.stg_cols != cols) m->tm_phi_ptr = nullptr;  // the Phi map's box follows the staging
+    }
     p.scan_threads = c.sw;
     p.proj_b_resident = c.br;
     p.use_theta_tc = c.tc;
@@ -1157,7 +1163,9 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
             std::istringstream is(line);
             int a, b, c, d, e;
             TuneCfg t;
-            if (is >> a >> b >> c >> d >> e >> t.ns_s >> t.ns_b >> t.sw >> t.br >> t.tc >> t.gs_ns >> t.nacc) {
+            std::string tag;  // lines of this format end in "s2"
+            if (is >> a >> b >> c >> d >> e >> t.ns_s >> t.sy >> t.sw >> t.br >> t.tc >> t.gs_ns >> t.nacc >> tag &&
+                tag == "s2") {
                 std::ostringstream k;
                 k << a << ' ' << b << ' ' << c << ' ' << d << ' ' << e;
                 // a line that does not fit this plan's reserved memory is not used
@@ -1221,28 +1229,26 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     std::vector<TuneCfg> cands;
     if (m->eff_prec != MP_PREC_FP64) {
         cands.clear();
-        for (int tc = 0; tc <= base.theta_tc_ok; ++tc) cands.push_back({best.ns_s, best.ns_b, best.sw, best.br, tc, best.gs_ns, best.nacc});
+        for (int tc = 0; tc <= base.theta_tc_ok; ++tc) cands.push_back({best.ns_s, best.sy, best.sw, best.br, tc, best.gs_ns, best.nacc});
         sweep(cands);
         if (best.tc) {
             cands.clear();
-            for (int ns : {8, 16, 32}) cands.push_back({best.ns_s, best.ns_b, best.sw, best.br, best.tc, ns, best.nacc});
+            for (int ns : {8, 16, 32}) cands.push_back({best.ns_s, best.sy, best.sw, best.br, best.tc, ns, best.nacc});
             sweep(cands);
         }
         cands.clear();
-        for (int na = 1; na <= base.proj_nacc_max; ++na) cands.push_back({best.ns_s, best.ns_b, best.sw, best.br, best.tc, best.gs_ns, na});
+        for (int na = 1; na <= base.proj_nacc_max; ++na) cands.push_back({best.ns_s, best.sy, best.sw, best.br, best.tc, best.gs_ns, na});
         sweep(cands);
         cands.clear();
         for (int ns_s = 2; ns_s <= base.ns_s_max; ns_s += 2)
-            for (int br = 0; br <= 1; ++br) cands.push_back({ns_s, best.ns_b, best.sw, br, best.tc, best.gs_ns, best.nacc});
+            for (int br = 0; br <= 1; ++br) cands.push_back({ns_s, best.sy, best.sw, br, best.tc, best.gs_ns, best.nacc});
         sweep(cands);
-        if (!base.b_resident) {
-            cands.clear();
-            for (int ns_b = 2; ns_b <= base.ns_b_max; ++ns_b) cands.push_back({best.ns_s, ns_b, best.sw, best.br, best.tc, best.gs_ns, best.nacc});
-            sweep(cands);
-        }
+        cands.clear();
+        for (int k = 0; k < synth_cfg_count(); ++k) cands.push_back({best.ns_s, k, best.sw, best.br, best.tc, best.gs_ns, best.nacc});
+        sweep(cands);
     }
     cands.clear();
-    for (int sw : {64, 128, 256}) cands.push_back({best.ns_s, best.ns_b, sw, best.br, best.tc, best.gs_ns, best.nacc});
+    for (int sw : {64, 128, 256}) cands.push_back({best.ns_s, best.sy, sw, best.br, best.tc, best.gs_ns, best.nacc});
     sweep(cands);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1258,8 +1264,8 @@ mp_status mp_autotune(mp_mesh *m, const char *cache_path)
     if (st != MP_OK) return st;
     if (cache_path) {
         std::ofstream f(cache_path, std::ios::app);
-        f << key << ' ' << best.ns_s << ' ' << best.ns_b << ' ' << best.sw << ' ' << best.br << ' ' << best.tc << ' '
-          << best.gs_ns << ' ' << best.nacc << '\n';
+        f << key << ' ' << best.ns_s << ' ' << best.sy << ' ' << best.sw << ' ' << best.br << ' ' << best.tc << ' '
+          << best.gs_ns << ' ' << best.nacc << " s2\n";
     }
     return mp_mesh_synchronize(m);
 }

@@ -40,7 +40,6 @@ struct SplitPlan {
     int ns_o = 2;         // projection: stages of converted A operands (bf16 terms)
     int proj_ns_b = 2;    // projection: table ring slots (when the table is not resident)
     int ns_s_max = 0;     // projection: the deepest density ring the reserved shared memory holds
-    int ns_b_max = 0;     // synthesis: the deepest table ring the reserved shared memory holds
     int proj_b_resident = 0;  // projection: whole pre-split table held in shared memory
     int proj_res_ok = 0, proj_ring_ok = 0;  // projection: which table modes fit the reserved memory
     int ns_b = 3;         // synthesis: table stages (when not resident)
@@ -48,6 +47,7 @@ struct SplitPlan {
     int b_resident = 0;   // synthesis: whole table held in shared memory
     int stg_bufs = 2;     // synthesis: TMA store staging boxes per epilogue warp
     int stg_cols = 16;    // synthesis: float64 columns of a staging box (16: 128B swizzle, 8: 64B)
+    int synth_cfg = 0;    // synthesis: index of the stage configuration above (synth_cfg_apply)
     int proj_nacc = 1;    // projection: accumulators per tile (K chunks dealt round-robin)
     int proj_nacc_max = 1;
     int scan_threads = 128;  // radial recurrences: threads (shell chunks) per moment column
@@ -247,6 +247,11 @@ cudaError_t launch_split_project(mp_mesh *m, const double *rho);
 cudaError_t launch_split_theta(mp_mesh *m);
 cudaError_t launch_split_synth(mp_mesh *m, double *phi);
 int split_smem_limits(mp_mesh *m);  // 0 when the plan fits, else an error
+// stage configurations of the phi synthesis (A stages, table residency / ring, staging boxes)
+int synth_cfg_count();
+bool synth_cfg_fits(const SplitPlan &pl, int k);
+void synth_cfg_apply(SplitPlan &pl, int k);
+std::vector<int> synth_cfg_order(const SplitPlan &pl);
 
 // ---- tensor-core theta stages (orders m >= 1)
 bool plan_theta_tc(mp_mesh *m, std::vector<unsigned long long> &th_off, size_t &th_bytes,

@@ -1177,6 +1177,59 @@ int synth_smem_bytes(const SplitPlan &pl, int ns_a, int b_slots, int stg_bufs, i
 
 }  // namespace
 
+namespace {
+
+// Stage configurations of the phi synthesis: A-operand stages, table resident or its ring
+// slots, staging boxes per epilogue warp and their columns (16: 128B swizzle, 8: 64B).
+struct SynthCfg {
+    int ns_a, resident, ns_b, stg, cols;
+};
+constexpr SynthCfg kSynthCfgs[] = {
+    {2, 1, 0, 2, 16}, {2, 0, 3, 2, 16}, {2, 0, 2, 2, 16}, {1, 0, 2, 2, 16},  // 8 KB of staging a warp
+    {2, 1, 0, 2, 8},  {2, 0, 3, 2, 8},  {2, 0, 2, 2, 8},  {1, 0, 2, 2, 8},   // 4 KB, double-buffered
+    {2, 0, 2, 1, 16}, {2, 0, 2, 1, 8},  {1, 0, 2, 1, 16}, {1, 0, 2, 1, 8},   // one box
+};
+
+}  // namespace
+
+int synth_cfg_count() { return (int)(sizeof(kSynthCfgs) / sizeof(kSynthCfgs[0])); }
+
+bool synth_cfg_fits(const SplitPlan &pl, int k)
+{
+    if (k < 0 || k >= synth_cfg_count()) return false;
+    const SynthCfg &c = kSynthCfgs[k];
+    const int b_slots = c.resident ? pl.n_nc * (pl.Kpad / 16) : c.ns_b;
+    return synth_smem_bytes(pl, c.ns_a, b_slots, c.stg, c.cols) <= kSmemLimit;
+}
+
+void synth_cfg_apply(SplitPlan &pl, int k)
+{
+    const SynthCfg &c = kSynthCfgs[k];
+    const int b_slots = c.resident ? pl.n_nc * (pl.Kpad / 16) : c.ns_b;
+    pl.synth_cfg = k;
+    pl.ns_a = c.ns_a;
+    pl.b_resident = c.resident;
+    pl.ns_b = c.resident ? 1 : c.ns_b;
+    pl.stg_bufs = c.stg;
+    pl.stg_cols = c.cols;
+    pl.synth_smem = synth_smem_bytes(pl, c.ns_a, b_slots, c.stg, c.cols);
+}
+
+// Preferred order of the synthesis stage configurations.  Where a tile's A operand is large
+// (>= 48 KB: l_max >= 48), a second A stage comes first, so the next unit's operand arrives
+// while the current one is multiplied; else the staging volume does.  Measured on GB300:
+// 2048 x 512 x 1024 cells at l_max = 64 (66.5 KB A stages) ran the synthesis in 1414 us with
+// two A stages beside one 8-column box a warp against 1553 us with one A stage beside two; a
+// log-normal 1024 x 256 x 512 mesh at l_max = 32 (33.8 KB) in 176 us with one A stage beside
+// two 16-column boxes against 189 us with four 8-column ones and 207 us with two A stages
+// beside two 8-column boxes.
+std::vector<int> synth_cfg_order(const SplitPlan &pl)
+{
+    const int a_stage = pl.a_terms * kBM * pl.Kpad * 2 + 1024;
+    if (a_stage >= 48 * 1024) return {0, 1, 2, 4, 5, 6, 8, 9, 3, 7, 10, 11};
+    return {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11};
+}
+
 // Chooses ring depths that fit shared memory; fills plan.* sizes.
 int split_smem_limits(mp_mesh *m)
 {
@@ -1206,30 +1259,11 @@ int split_smem_limits(mp_mesh *m)
         }
     }
     if (ns_s == 0) return 1;
-    // synthesis: 8 KB of staging per epilogue warp (two boxes of 16 columns), then double-buffered
-    // 4 KB (two boxes of 8 columns), then a single box; within each, the whole table resident and
-    // two A stages first.  Measured on GB300: a log-normal 1024 x 256 x 512, l_max = 32 mesh ran
-    // it in 176 us with one A stage beside two 16-column boxes, 189 us with four 8-column ones
-    // and 207 us with two A stages and a three-slot table ring beside two 8-column ones; the
-    // 2048 x 512 x 1024, l_max = 64 mesh, where only 4 KB fit, in 1551 us with two 8-column boxes
-    // against 1565 us with one 16-column box.
-    const int n_chunks = pl.n_nc * (pl.Kpad / 16);
-    struct Cfg {
-        int ns_a, resident, ns_b, stg, cols;
-    };
-    const Cfg cfgs[] = {{2, 1, 0, 2, 16}, {2, 0, 3, 2, 16}, {2, 0, 2, 2, 16}, {1, 0, 2, 2, 16},
-                        {2, 1, 0, 2, 8},  {2, 0, 3, 2, 8},  {2, 0, 2, 2, 8},  {1, 0, 2, 2, 8},
-                        {2, 0, 2, 1, 16}, {1, 0, 2, 1, 16}};
+    // synthesis: the first stage configuration of the preferred order that fits
     bool found = false;
-    for (const Cfg &c : cfgs) {
-        const int b_slots = c.resident ? n_chunks : c.ns_b;
-        if (synth_smem_bytes(pl, c.ns_a, b_slots, c.stg, c.cols) <= kSmemLimit) {
-            pl.ns_a = c.ns_a;
-            pl.b_resident = c.resident;
-            pl.ns_b = c.resident ? 1 : c.ns_b;
-            pl.stg_bufs = c.stg;
-            pl.stg_cols = c.cols;
-            pl.synth_smem = synth_smem_bytes(pl, c.ns_a, b_slots, c.stg, c.cols);
+    for (int k : synth_cfg_order(pl)) {
+        if (synth_cfg_fits(pl, k)) {
+            synth_cfg_apply(pl, k);
             found = true;
             break;
         }
@@ -1237,7 +1271,6 @@ int split_smem_limits(mp_mesh *m)
     if (!found) return 2;
     pl.ns_s = ns_s;
     pl.ns_s_max = ns_s;
-    pl.ns_b_max = pl.ns_b;
     pl.ns_o = ns_o;
     pl.proj_ns_b = ns_bp;
     pl.proj_b_resident = b_res;
