@@ -221,8 +221,11 @@ __global__ void __launch_bounds__(NT) k_scan_reg(const double *__restrict__ A, c
 // c = t >> 2, so the four columns of a shell row sit in one 32-byte sector of A, MR, MI
 // and C (one column per block reads a quarter of every sector it touches).  The block
 // scans run over the lanes of one column (stride 4 within a warp), then over the warps.
+// (two blocks per SM: the kernel is latency-bound, and the second block hides more of it
+// than the registers the cap takes away; at 2048 shells, CH = 16, with a few spills to
+// local memory: 226 -> 207 us against one block of 124 registers per SM)
 template <int NT, int CH>
-__global__ void __launch_bounds__(4 * NT) k_scan_q4(const double *__restrict__ A, const double *__restrict__ WR,
+__global__ void __launch_bounds__(4 * NT, 2) k_scan_q4(const double *__restrict__ A, const double *__restrict__ WR,
                                                     const double *__restrict__ WI, const double *__restrict__ GR,
                                                     const double *__restrict__ GI, double *__restrict__ MR,
                                                     double *__restrict__ MI, double *__restrict__ C,
