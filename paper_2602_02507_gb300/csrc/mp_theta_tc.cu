@@ -529,22 +529,34 @@ __global__ void __launch_bounds__(256) k_theta_m0(const ThetaTcParams prm)
     const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
     const int i0 = blockIdx.x * kM0Shells, l0 = blockIdx.y * kM0Deg;
     float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int j0 = 0; j0 < prm.n_t; j0 += kM0K) {
-        __syncthreads();  // the previous chunk is consumed
-        for (int e = tid; e < kM0Deg * (kM0K / 4); e += 256) {
-            const int r = e >> 3, q = e & 7, l = l0 + r, j = j0 + 4 * q;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the next chunk's table and F values are loaded into registers while this chunk is
+    // summed (two table float4s and, for the first 128 threads, one F float4 a thread)
+    float4 tv[2], fv = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto load = [&](int j0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int e = tid + 256 * k, r = e >> 3, q = e & 7, l = l0 + r, j = j0 + 4 * q;
+            tv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (l <= prm.L && j < prm.ldF)
-                v = __ldg(reinterpret_cast<const float4 *>(prm.Ith32 + (size_t)tri(l, 0) * prm.ldF + j));
-            *reinterpret_cast<float4 *>(&sT[r][4 * q]) = v;
+                tv[k] = __ldg(reinterpret_cast<const float4 *>(prm.Ith32 + (size_t)tri(l, 0) * prm.ldF + j));
         }
         if (tid < kM0Shells * (kM0K / 4)) {
             const int r = tid >> 3, q = tid & 7, i = i0 + r, j = j0 + 4 * q;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < prm.n_r && j < prm.ldF) v = __ldg(reinterpret_cast<const float4 *>(prm.F + (size_t)i * prm.P * prm.ldF + j));
-            *reinterpret_cast<float4 *>(&sF[r][4 * q]) = v;
+            fv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < prm.n_r && j < prm.ldF) fv = __ldg(reinterpret_cast<const float4 *>(prm.F + (size_t)i * prm.P * prm.ldF + j));
         }
+    };
+    load(0);
+    for (int j0 = 0; j0 < prm.n_t; j0 += kM0K) {
+        __syncthreads();  // the previous chunk is consumed
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int e = tid + 256 * k;
+            *reinterpret_cast<float4 *>(&sT[e >> 3][4 * (e & 7)]) = tv[k];
+        }
+        if (tid < kM0Shells * (kM0K / 4)) *reinterpret_cast<float4 *>(&sF[tid >> 3][4 * (tid & 7)]) = fv;
         __syncthreads();
+        if (j0 + kM0K < prm.n_t) load(j0 + kM0K);
 #pragma unroll
         for (int jb = 0; jb < kM0K; jb += 8) {
             const float4 f0 = *reinterpret_cast<const float4 *>(&sF[cg][jb]);
