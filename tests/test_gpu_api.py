@@ -254,6 +254,41 @@ def test_profile_names_every_kernel(engine):
     assert all(v["launches"] == 3 and v["total_ms"] > 0 for v in prof.values())
 
 
+@pytest.mark.parametrize("shape,L", [((32, 32, 64), 8), ((32, 64, 512), 40)])
+def test_every_synthesis_stage_configuration_matches_the_oracle(tmp_path, shape, L):
+    """Each stage configuration of the phi synthesis (A stages, table residency or ring,
+    staging boxes of 16 or 8 columns), applied through a tuner cache line, against the
+    oracle.  Lines that do not fit a mesh's shared memory are not applied (the tuner then
+    times candidates instead), and are skipped here.  The radial range keeps neighbouring
+    edges within a factor 1.05 (the midpoint split weighs a shell's own degree-l moment by
+    (r_{i+1}/r_i)^l, which at l = 40 and a factor 2 would leave no digit to compare)."""
+    import torch
+    from paper_2602_02507_gb300 import multipole as mpl
+    w = W.presn(n_r=shape[0], n_theta=shape[1], n_phi=shape[2], L=L, r_lo=1e7, r_hi=4e7)
+    m = w.mesh
+    ref = oracle_solve(w)["phi"]
+    rho = torch.from_numpy(w.rho).cuda()
+    phi = torch.empty_like(rho)
+    applied = 0
+    for sy in range(12):
+        cache = tmp_path / f"tune_{sy}.txt"
+        with mpl.Mesh(m.r, m.theta, m.phi, m.L, m.G, precision="bf16x3") as mesh:
+            # key (n_r n_theta n_phi l_max precision), then ns_s sy sw br tc gs_ns nacc, format tag
+            cache.write_text(f"{shape[0]} {shape[1]} {shape[2]} {L} 1 2 {sy} 128 0 1 8 1 s2\n")
+            mesh.set_density(rho)
+            mesh.set_phi_output(phi)
+            mesh.autotune(str(cache))
+            if mesh.info()["tuned_candidates"] != 0:
+                continue  # this configuration does not fit the mesh
+            applied += 1
+            phi.fill_(float("nan"))
+            mesh.solve()
+            mesh.synchronize()
+            err = phi_rel_err(phi.cpu().numpy(), ref)
+            assert err <= 1e-6, (sy, err)
+    assert applied >= 6, applied
+
+
 def test_autotune_keeps_results(tmp_path):
     import torch
     from paper_2602_02507_gb300 import multipole as mpl
