@@ -281,12 +281,17 @@ MP_API mp_status mp_batch_destroy(mp_batch *batch);
 
 /*
  * Pick launch parameters for the mesh by timing candidates on the device
- * (needs a bound density): the projection's density ring depth and table
- * residency, the synthesis table ring depth (when the table is not resident),
- * the threads per moment column of the radial recurrences and the engine of the
- * theta stages (tensor cores or CUDA cores, see mp_set_theta_engine).  The choice is cached in
- * cache_path (a text file, may be NULL) keyed by (n_r, n_theta, n_phi, l_max,
- * precision) and reused by later meshes of the same key.
+ * (needs a bound density).  Swept: the projection's density ring depth, its
+ * table residency and its number of TMEM accumulators; the phi synthesis's
+ * stage configuration (A-operand stages, table residency or ring depth, and
+ * the count and width of its output staging boxes); the threads per moment
+ * column of the radial recurrences; the engine of the theta stages (tensor
+ * cores or CUDA cores, see mp_set_theta_engine) and the shells per unit of
+ * the tensor-core theta synthesis.  The choice is cached in cache_path (a
+ * text file, may be NULL; one line per mesh key, ending in the format tag
+ * "s2", lines of other formats ignored) keyed by (n_r, n_theta, n_phi, l_max,
+ * precision) and reused by later meshes of the same key.  A cached line that
+ * does not fit the mesh's plan is skipped, and the candidates are timed anew.
  */
 MP_API mp_status mp_autotune(mp_mesh *mesh, const char *cache_path);
 
