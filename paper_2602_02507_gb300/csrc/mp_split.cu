@@ -20,7 +20,8 @@
 // tcgen05.ld, get the m = 0 term added, become float64 with integer ops and
 // leave through TMA stores.
 //
-// Roles per CTA (persistent, one CTA per SM): warp 0 issues TMA / bulk copies,
+// Roles per CTA (persistent, one CTA per SM): warp 0 issues the TMA / bulk copies
+// of the streamed operand (the projection's table chunks come from warp 2),
 // warp 1 owns tensor memory and issues the MMAs, the other warps convert and
 // run the epilogues.  Every mbarrier wait is bounded (ptx.cuh).
 #include <cstdio>
@@ -76,12 +77,12 @@ struct ProjParams {
     uint32_t bload;        // bytes of the terms the products read (a prefix of the chunk)
 };
 
-// Converter warps: two groups of kGroupWarps; group g converts the chunks whose
-// CTA-wide sequence number c has c % 2 == g, so that each SM sub-partition holds
+// Converter warps (warps 3 ..): two groups of kGroupWarps; group g converts the chunks
+// whose CTA-wide sequence number c has c % 2 == g, so that each SM sub-partition holds
 // four converter warps (their integer conversion chains hide each other's latency).
 constexpr int kGroupWarps = 8;
 constexpr int kProjConvWarps = 2 * kGroupWarps;
-constexpr int kProjThreads = (2 + kProjConvWarps) * 32;
+constexpr int kProjThreads = (3 + kProjConvWarps) * 32;
 
 template <int A_TERMS, int NPROD>
 __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_constant__ CUtensorMap tmS,
@@ -153,9 +154,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
     pdl_wait();
 
     if (warp == 0) {
-        // ---------------- producers: lane 0 streams the two TMA boxes of rho per chunk; lane 16
-        // the table chunks on a ring of their own (when the table is not resident), so that a
-        // shallow table ring does not hold back the density prefetch
+        // ---------------- density producer: lane 0 streams the two TMA boxes of rho per chunk
         if (lane == 0) {
             tma_prefetch_desc(&tmS);
             // rho is read once per solve: its lines go first, ahead of F, tables and moments
@@ -183,7 +182,14 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                 while (!mbar_try_wait(smem_u32(&b_full[0]), 0) && clock64() - t0 < MP_WAIT_BUDGET_CYCLES) {
                 }
             }
-        } else if (lane == 16 && !prm.b_resident) {
+        }
+    } else if (warp == 2) {
+        // ---------------- table producer (when the table is not resident): the table chunks on a
+        // ring of their own, so that a shallow table ring does not hold back the density
+        // prefetch.  A warp of its own: beside the density producer in one warp, each lane's
+        // blocking barrier waits held up the other's copies (1567 -> 1525 us per launch at
+        // 2048 x 512 x 1024 cells, l_max = 64)
+        if (lane == 0 && !prm.b_resident) {
             Ring rb;
             int issued_b = 0;
             for (int tile = blockIdx.x; tile < prm.n_tiles && !*abort_flag; tile += gridDim.x) {
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         }
     } else {
         // ---------------- converters + epilogue
-        const int cw = warp - 2, grp = cw / kGroupWarps, qd = warp & 3, half = (cw >> 2) & 1;
+        const int cw = warp - 3, grp = cw / kGroupWarps, qd = warp & 3, half = (cw >> 2) & 1;
         const int row = qd * 32 + lane;
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
         int lt = 0, prev_tile = -1;
