@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
         const int cw = warp - 3, grp = cw / kGroupWarps, qd = warp & 3, half = (cw >> 2) & 1;
         const int row = qd * 32 + lane;
         const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
-        int lt = 0, prev_tile = -1;
+        int lt = 0;
         // this group converts the chunks c = grp, grp + 2, ... of the CTA-wide sequence (the
         // producer's and the MMA's order): its ring positions advance two slots per own chunk
         Ring rs, ro;
@@ -267,44 +267,78 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
             ro.next(NS_O);
         }
         int par = 0;  // parity of the CTA-wide chunk sequence number
-        float sref = 0.0f, sref_prev = 0.0f;
+        float sref = 0.0f;
         uint32_t efmax = 0;  // largest float64 exponent field seen (flags values beyond float32)
         bool ok = true;
 
-        // the accumulator of a finished tile: F = D + sref colsum, stored per shell as rows of
+        // The accumulator of a finished tile: F = D + sref colsum, stored per shell as rows of
         // polar cells (lanes hold consecutive cells: each store is coalesced); column groups
-        // split four ways
-        auto epilogue = [&](int etile, int elt, float sr) -> bool {
-            const int b = elt & 1;
-            bool w_ok = warp_all(mbar_wait(smem_u32(&acc_full[b]), (elt >> 1) & 1, abort_flag, prm.err));
-            if (!w_ok) return false;
-            tc_fence_after();
-            const long long grow = (long long)etile * kBM + row;
-            const long long ish = grow / prm.n_t;
-            float *fdst = prm.F + (size_t)ish * prm.P * prm.ldF + (grow - ish * prm.n_t);
-            const int ngroups = Npad / 8;
-            for (int cg = 2 * grp + half; cg < ngroups && cg * 8 < prm.P; cg += 4) {
-                uint32_t v[4][8];
+        // split four ways.  A tile's epilogue runs in steps of one column group, between the
+        // own chunks of the next tile (from its second on, when the tile's last MMAs have
+        // completed), so that the converters never leave the MMAs and the density ring idle
+        // for a whole epilogue; what is left runs at the end of that tile.  Measured on GB300
+        // at 2048 x 512 x 1024 cells, l_max = 64: 1537 -> 1447 us per launch against the
+        // whole epilogue after each tile.
+        struct {
+            int tile = -1, lt = 0, cg = 0;
+            float sr = 0.0f;
+            bool ready = false;  // the tile's accumulator is complete
+        } ep;
+        const int ngroups = Npad / 8;
+        auto ep_more = [&]() { return ep.cg < ngroups && ep.cg * 8 < prm.P; };
+        auto ep_step = [&]() -> bool {
+            if (ep.tile < 0) return true;
+            const int b = ep.lt & 1;
+            if (!ep.ready) {
+                // also before a warp with no column group arrives: an arrival on acc_empty may
+                // only follow the completion of this tile's MMAs, which follow every warp's
+                // arrival for the buffer's previous tile
+                if (!warp_all(mbar_wait(smem_u32(&acc_full[b]), (ep.lt >> 1) & 1, abort_flag, prm.err))) return false;
+                tc_fence_after();
+                ep.ready = true;
+            }
+            if (ep_more()) {
+                const long long grow = (long long)ep.tile * kBM + row;
+                const long long ish = grow / prm.n_t;
+                float *fdst = prm.F + (size_t)ish * prm.P * prm.ldF + (grow - ish * prm.n_t);
+                const int cg = ep.cg;
                 const uint32_t col = tmem_base + lane_base + (uint32_t)b * acc_stride + (uint32_t)(cg * 8);
+                // one accumulator at a time: these steps sit inside the conversion loop, whose
+                // registers they must not crowd out
+                float acc[8];
+                {
+                    uint32_t v[8];
+                    tmem_ld8(col, v);
+                    tmem_ld_wait();
 #pragma unroll
-                for (int s = 0; s < 4; ++s)
-                    if (s < nacc) tmem_ld8(col + (uint32_t)(s * Npad), v[s]);
-                tmem_ld_wait();
+                    for (int e = 0; e < 8; ++e) acc[e] = __uint_as_float(v[e]);
+                    for (int s = 1; s < nacc; ++s) {
+                        tmem_ld8(col + (uint32_t)(s * Npad), v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) acc[e] += __uint_as_float(v[e]);
+                    }
+                }
                 if (grow < prm.R) {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
-                        float acc = __uint_as_float(v[0][e]);
-#pragma unroll
-                        for (int s = 1; s < 4; ++s)
-                            if (s < nacc) acc += __uint_as_float(v[s][e]);
                         const int p = cg * 8 + e;
-                        if (p < prm.P) fdst[(size_t)p * prm.ldF] = fmaf(sr, prm.colsum[p], acc);
+                        if (p < prm.P) fdst[(size_t)p * prm.ldF] = fmaf(ep.sr, prm.colsum[p], acc[e]);
                     }
                 }
+                ep.cg += 4;
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+            if (!ep_more()) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+                ep.tile = -1;
+            }
+            return true;
+        };
+        auto ep_finish = [&]() -> bool {
+            while (ep.tile >= 0)
+                if (!ep_step()) return false;
             return true;
         };
 
@@ -325,6 +359,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                 ref_next = load_ref(tile + gridDim.x);
             }
             const int rot = rotated_chunk(0, tile, prm.n_kc);
+            int own = 0;  // own chunks of this tile so far
             for (int it = 0; it < prm.n_kc; ++it, par ^= 1) {
                 if (par != grp) continue;
                 const int kc = (it + rot >= prm.n_kc) ? it + rot - prm.n_kc : it + rot;
@@ -411,13 +446,21 @@ __global__ void __launch_bounds__(kProjThreads, 1) k_proj_tc(const __grid_consta
                     mbar_arrive(smem_u32(&s_empty[sidx]));
                     mbar_arrive(smem_u32(&o_full[oidx]));
                 }
+                if (own++ >= 1) {
+                    ok = ep_step();
+                    if (!ok) break;
+                }
             }
             if (!ok) break;
-            if (prev_tile >= 0) ok = epilogue(prev_tile, lt - 1, sref_prev);
-            prev_tile = tile;
-            sref_prev = sref;
+            ok = ep_finish();
+            if (!ok) break;
+            ep.tile = tile;
+            ep.lt = lt;
+            ep.sr = sref;
+            ep.cg = 2 * grp + half;
+            ep.ready = false;
         }
-        if (ok && prev_tile >= 0) epilogue(prev_tile, lt - 1, sref_prev);
+        if (ok) ep_finish();
         // exponent fields above float32's range (including inf / nan, 0x7FF) are reported
         if (efmax > (1150u << 20)) atomicOr(prm.err, DEV_ERR_NONFINITE);
     }
