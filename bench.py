@@ -101,8 +101,8 @@ def dist_info():
 
 
 def measured_peaks():
-    """(HBM GB/s, bf16 TFLOP/s sustained, kind): the measured peaks of this machine's
-    GB300s, else the fallback figures."""
+    """(HBM GB/s, bf16 TFLOP/s sustained, kind): the peaks measured on these GB300s
+    (MEASURED_PEAKS.json: a copy stream and a bf16 GEMM), else fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
