@@ -85,6 +85,11 @@ SPLIT_CASES = {
                                    ("bf16x3",)),
     # more 128-row tiles than the projection's persistent grid has CTAs, the last tile ragged
     "multi_wave_200x100x32_L8": (lambda: W.presn(n_r=200, n_theta=100, n_phi=32, L=8), ("bf16x3", "bf16x6")),
+    # three tiles per CTA of the projection, three K chunks per tile (the two converter groups
+    # take one or two chunks of a tile, alternately) and three accumulators per tile: the
+    # epilogue steps of a tile interleave with the next tile's chunks or run at its end
+    "odd_chunks_3_tiles_per_cta_456x128x96_L12": (lambda: W.presn(n_r=456, n_theta=128, n_phi=96, L=12),
+                                                  ("bf16x3",)),
     # tables too large for shared memory: the direct theta contraction and the per-row
     # theta synthesis
     "high_L_fallback_4x96x64_L30": (lambda: W.presn(n_r=4, n_theta=96, n_phi=64, L=30, r_lo=1e7, r_hi=1.3e7),
