@@ -895,7 +895,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
             int issued_a = 0, issued_b = 0;
             for (int unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x, ra.next(NS_A)) {
                 const int tile = unit / prm.n_nc, nc = unit - tile * prm.n_nc;
-                ok = mbar_wait(smem_u32(&a_empty[ra.idx]), ra.phase ^ 1, abort_flag, prm.err, true);
+                ok = mbar_wait(smem_u32(&a_empty[ra.idx]), ra.phase ^ 1, abort_flag, prm.err);
                 if (!ok) break;
                 const uint32_t fb = smem_u32(&a_full[ra.idx]);
                 uint8_t *dst = sA + (size_t)ra.idx * a_stage;
@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                 ++issued_a;
                 if (!prm.b_resident) {
                     for (int c = nc * nkk; c < (nc + 1) * nkk && ok; ++c, rb.next(NS_B)) {
-                        ok = mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err, true);
+                        ok = mbar_wait(smem_u32(&b_empty[rb.idx]), rb.phase ^ 1, abort_flag, prm.err);
                         if (!ok) break;
                         mbar_arrive_expect_tx(smem_u32(&b_full[rb.idx]), prm.bload);
                         bulk_load(smem_u32(sB + (size_t)rb.idx * prm.bload), prm.tabT + (size_t)c * prm.bchunk,
@@ -937,16 +937,16 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
             Ring ra, rb;
             uint32_t u = 0;
             bool ok = true;
-            if (prm.b_resident && blockIdx.x < n_units) ok = mbar_wait(smem_u32(&b_full[0]), 0, abort_flag, prm.err, true);
+            if (prm.b_resident && blockIdx.x < n_units) ok = mbar_wait(smem_u32(&b_full[0]), 0, abort_flag, prm.err);
             for (int unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x, ra.next(NS_A)) {
                 const int nc = unit % prm.n_nc;
-                ok = mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err, true);
+                ok = mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t a_base0 = smem_u32(sA + (size_t)ra.idx * a_stage);
                 {
                     const int buf = u & 1;
-                    ok = mbar_wait(smem_u32(&acc_empty[buf]), ((u >> 1) & 1) ^ 1, abort_flag, prm.err, true);
+                    ok = mbar_wait(smem_u32(&acc_empty[buf]), ((u >> 1) & 1) ^ 1, abort_flag, prm.err);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)buf * acc_stride;
@@ -955,7 +955,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
                         if (prm.b_resident) {
                             b_base = smem_u32(sB + (size_t)(nc * nkk + kk) * prm.bload);
                         } else {
-                            ok = mbar_wait(smem_u32(&b_full[rb.idx]), rb.phase, abort_flag, prm.err, true);
+                            ok = mbar_wait(smem_u32(&b_full[rb.idx]), rb.phase, abort_flag, prm.err);
                             if (!ok) break;
                             tc_fence_after();
                             b_base = smem_u32(sB + (size_t)rb.idx * prm.bload);
@@ -1000,7 +1000,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
         for (int unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x, ra.next(NS_A)) {
             const int tile = unit / prm.n_nc, nc = unit - tile * prm.n_nc;
             const int rot = nmine > 0 ? rotated_chunk(0, tile, nmine) : 0;
-            ok = warp_all(mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err, true));
+            ok = warp_all(mbar_wait(smem_u32(&a_full[ra.idx]), ra.phase, abort_flag, prm.err));
             if (!ok) break;
             const float2 g0 = reinterpret_cast<const float2 *>(sA + (size_t)ra.idx * a_stage + prm.a_bytes)[row];
             // the stage is refilled by the bulk-copy engine (the async proxy): the m = 0 values just
@@ -1012,7 +1012,7 @@ __global__ void __launch_bounds__(synth::THREADS, 1)
             const bool box_valid = box_row < prm.R;
             {
                 const int buf = u & 1;
-                ok = warp_all(mbar_wait(smem_u32(&acc_full[buf]), (u >> 1) & 1, abort_flag, prm.err, true));
+                ok = warp_all(mbar_wait(smem_u32(&acc_full[buf]), (u >> 1) & 1, abort_flag, prm.err));
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t tcol = tmem_base + lane_base + (uint32_t)buf * acc_stride;

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(thc::THREADS, 1) k_theta_tc(const __grid_const
                 const uint32_t tb = (uint32_t)(prm.bterms * Nm * 64);
                 const uint8_t *tsrc = prm.tab + prm.off[m];
                 for (int c = 0; c < prm.n_kc; ++c, rs.next(NS_S)) {
-                    ok = mbar_wait(smem_u32(&s_empty[rs.idx]), rs.phase ^ 1, abort_flag, prm.err, true);
+                    ok = mbar_wait(smem_u32(&s_empty[rs.idx]), rs.phase ^ 1, abort_flag, prm.err);
                     if (!ok) break;
                     const uint32_t fb = smem_u32(&s_full[rs.idx]);
                     const uint32_t dst = smem_u32(sS + (size_t)rs.idx * prm.stage_bytes);
@@ -154,13 +154,13 @@ __global__ void __launch_bounds__(thc::THREADS, 1) k_theta_tc(const __grid_const
                 const uint32_t idesc = idesc_bf16_f32(128, Nm);
                 const uint32_t b_term = (uint32_t)Nm * 64;
                 const int b = lt & 1;
-                ok = mbar_wait(smem_u32(&acc_empty[b]), ((lt >> 1) & 1) ^ 1, abort_flag, prm.err, true);
+                ok = mbar_wait(smem_u32(&acc_empty[b]), ((lt >> 1) & 1) ^ 1, abort_flag, prm.err);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t d_buf = tmem_base + (uint32_t)b * acc_stride;
                 for (int c = 0; c < prm.n_kc; ++c, rs.next(NS_S), ro.next(NS_O)) {
-                    ok = mbar_wait(smem_u32(&o_full[ro.idx]), ro.phase, abort_flag, prm.err, true) &&
-                         mbar_wait(smem_u32(&s_full[rs.idx]), rs.phase, abort_flag, prm.err, true);
+                    ok = mbar_wait(smem_u32(&o_full[ro.idx]), ro.phase, abort_flag, prm.err) &&
+                         mbar_wait(smem_u32(&s_full[rs.idx]), rs.phase, abort_flag, prm.err);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t a_base = smem_u32(sA + (size_t)ro.idx * A_TERMS * A_TERM_BYTES);
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(thc::THREADS, 1) k_theta_tc(const __grid_const
 
         auto epilogue = [&](int eu, int elt) -> bool {
             const int b = elt & 1;
-            if (!warp_all(mbar_wait(smem_u32(&acc_full[b]), (elt >> 1) & 1, abort_flag, prm.err, true))) return false;
+            if (!warp_all(mbar_wait(smem_u32(&acc_full[b]), (elt >> 1) & 1, abort_flag, prm.err))) return false;
             tc_fence_after();
             const int m = 1 + eu / prm.n_groups, g = eu - (m - 1) * prm.n_groups;
             const int Nm = round16(prm.L + 1 - m);
@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(thc::THREADS, 1) k_theta_tc(const __grid_const
                 rs.next(NS_S);
                 ro.next(NS_O);
                 ro.next(NS_O);
-                ok = warp_all(mbar_wait(smem_u32(&s_full[sidx]), sph, abort_flag, prm.err, true));
+                ok = warp_all(mbar_wait(smem_u32(&s_full[sidx]), sph, abort_flag, prm.err));
                 if (!ok) break;
-                ok = warp_all(mbar_wait(smem_u32(&o_empty[oidx]), oph ^ 1, abort_flag, prm.err, true));
+                ok = warp_all(mbar_wait(smem_u32(&o_empty[oidx]), oph ^ 1, abort_flag, prm.err));
                 if (!ok) break;
                 // this thread's 16 polar cells [16 half, 16 half + 16) of its row, 128B-swizzled
                 const uint8_t *src = sS + (size_t)sidx * prm.stage_bytes + (row >> 6) * BOX_BYTES + (row & 63) * 128;
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(gsc::THREADS, 1) k_gsynth_tc(const GsynthTcPar
                     const uint8_t *tsrc = prm.tab + prm.toff[m] + (size_t)jb * n_kcm * 3 * T_TERM_BYTES;
                     const uint8_t *csrc = prm.cb + prm.coff[m] + (size_t)sg * n_kcm * A_TERMS * c_term;
                     for (int kc = 0; kc < n_kcm; ++kc, rs.next(NS_S)) {
-                        ok = mbar_wait(smem_u32(&s_empty[rs.idx]), rs.phase ^ 1, abort_flag, prm.err, true);
+                        ok = mbar_wait(smem_u32(&s_empty[rs.idx]), rs.phase ^ 1, abort_flag, prm.err);
                         if (!ok) break;
                         const uint32_t fb = smem_u32(&s_full[rs.idx]);
                         const uint32_t dst = smem_u32(sS + (size_t)rs.idx * prm.stage_bytes);
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(gsc::THREADS, 1) k_gsynth_tc(const GsynthTcPar
             for (int u = blockIdx.x; u < prm.n_units && ok; u += gridDim.x, ++lt) {
                 const int mg = u / prm.n_jb / prm.n_sg;
                 const int b = lt & 1;
-                ok = mbar_wait(smem_u32(&acc_empty[b]), ((lt >> 1) & 1) ^ 1, abort_flag, prm.err, true);
+                ok = mbar_wait(smem_u32(&acc_empty[b]), ((lt >> 1) & 1) ^ 1, abort_flag, prm.err);
                 if (!ok) break;
                 tc_fence_after();
                 for (int ml = 0; ml < ORDERS && ok; ++ml) {
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(gsc::THREADS, 1) k_gsynth_tc(const GsynthTcPar
                     const int n_kcm = (prm.L + 1 - m + BK - 1) / BK;
                     const uint32_t d_tmem = tmem_base + (uint32_t)b * acc_stride + (uint32_t)(ml * N);
                     for (int kc = 0; kc < n_kcm; ++kc, rs.next(NS_S)) {
-                        ok = mbar_wait(smem_u32(&s_full[rs.idx]), rs.phase, abort_flag, prm.err, true);
+                        ok = mbar_wait(smem_u32(&s_full[rs.idx]), rs.phase, abort_flag, prm.err);
                         if (!ok) break;
                         tc_fence_after();
                         const uint32_t t_base = smem_u32(sS + (size_t)rs.idx * prm.stage_bytes);
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(gsc::THREADS, 1) k_gsynth_tc(const GsynthTcPar
             const int jb = u % prm.n_jb, rest = u / prm.n_jb;
             const int sg = rest % prm.n_sg, mg = rest / prm.n_sg;
             const int b = lt & 1;
-            if (!warp_all(mbar_wait(smem_u32(&acc_full[b]), (lt >> 1) & 1, abort_flag, prm.err, true))) break;
+            if (!warp_all(mbar_wait(smem_u32(&acc_full[b]), (lt >> 1) & 1, abort_flag, prm.err))) break;
             tc_fence_after();
             const int j = jb * 128 + qd * 32 + lane;
             for (int sq = 0; sq < half_ns; sq += 4) {

@@ -57,22 +57,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// The same test with a suspend-time hint: a thread whose phase is not complete sleeps
-// until it completes (or 10 ms pass) instead of returning at once, which leaves the issue
-// slots of its sub-partition to the warps with work.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(10000000u)
-        : "memory");
-    return ok != 0;
-}
-
 // Bounded wait.  Returns false (after raising the CTA's abort flag and the
 // mesh error word) when the phase does not complete within the budget, or
 // when another role of the CTA already aborted.
@@ -90,18 +74,13 @@ __device__ __forceinline__ long long wait_budget(const int *err)
     return b > 0 ? b : MP_WAIT_BUDGET_CYCLES;
 }
 
-// sleep: use the sleeping test (measured on GB300 at 2048 x 512 x 1024 cells: 4 to 6 us
-// faster per launch in the phi synthesis and both tensor-core theta stages, 5 us slower
-// in the projection, which therefore keeps the plain test).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err,
-                                          bool sleep = false)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err)
 {
-    auto test = [&]() { return sleep ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity); };
-    if (test()) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     const long long budget = wait_budget(err);
     while (true) {
-        if (test()) return true;
+        if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
         if (clock64() - t0 > budget) {
             *abort_flag = 1;
